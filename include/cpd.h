@@ -1,0 +1,228 @@
+/*
+ * cpd.h — C ABI of the GB300 (sm_103a) CPD library: truncated MLSVD
+ * compression followed by damped Gauss-Newton (dGN) on the compressed core,
+ * after F. Bottega Diniz, "Tensor decompositions and algorithms, with
+ * applications to tensor learning" (thesis, 2019; arXiv 2110.05997).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Tensors are dense and column-major: entry (i1, ..., iL) (0-based) sits at
+ *    i1 + I1*(i2 + I2*(i3 + ...)), i.e. i1 fastest, the order in which the
+ *    thesis unfolds tensors (Sec. 1.2, Algorithm "Unfolding").
+ *  - A CPD with factors W^(l) (I_l x R, column-major) is passed as ONE buffer
+ *    holding vec(W^(1)), ..., vec(W^(L)) back to back: the stacked parameter
+ *    vector w of Sec. 3.1.  Block l starts at R * (I_1 + ... + I_{l-1}).
+ *  - Every tensor / factor / output pointer is a DEVICE pointer owned by the
+ *    caller; the library never allocates, frees or retains caller memory.
+ *    Scratch memory is the caller's `workspace` of at least the number of
+ *    bytes cpd_workspace_size() returns (256-byte aligned).
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = the
+ *    legacy default stream).  Calls that fill a host `cpd_info` synchronise
+ *    that stream before returning; everything else is stream-ordered.
+ *  - Arguments are validated before anything is launched; a validation
+ *    failure returns CPD_ERR_INVALID_ARG or CPD_ERR_UNSUPPORTED and touches
+ *    nothing.  A CUDA error returns CPD_ERR_CUDA.  Non-convergence is not an
+ *    error: it is stop_reason CPD_STOP_MAXITER.  NaN/Inf met during the
+ *    iteration ends it with info.status = CPD_ERR_NUMERIC.
+ *  - Distinct workspaces make concurrent calls on distinct streams safe.
+ *  - Supported orders: L = 3 and L = 4.  Ranks 1 <= R <= 64.
+ */
+#ifndef CPD_H_
+#define CPD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPD_MAX_ORDER 4
+#define CPD_MAX_RANK 64
+
+typedef enum {
+  CPD_OK = 0,
+  CPD_ERR_INVALID_ARG = -1,
+  CPD_ERR_CUDA = -2,
+  CPD_ERR_WORKSPACE = -3,
+  CPD_ERR_NUMERIC = -4,
+  CPD_ERR_TIMEOUT = -5,
+  CPD_ERR_UNSUPPORTED = -6
+} cpd_status;
+
+/* Stop tests of Sec. 4.1.3 ("Stopping conditions"), in the printed order. */
+typedef enum {
+  CPD_STOP_NONE = 0,
+  CPD_STOP_REL_ERR = 1,          /* ||S - S_k|| / ||S|| < tol               */
+  CPD_STOP_STEP = 2,             /* ||w_{k-1} - w_k|| < tol                 */
+  CPD_STOP_IMPROVEMENT = 3,      /* |e_{k-1} - e_k| < tol                   */
+  CPD_STOP_GRAD = 4,             /* ||grad F||_inf < tol                    */
+  CPD_STOP_AVG_ERR = 5,          /* windowed average error stalls           */
+  CPD_STOP_AVG_IMPROVEMENT = 6,  /* windowed improvement < 1e-3 * error     */
+  CPD_STOP_DIVERGENCE = 7,       /* e_k > max(1,||S||^2) / (1e-16 + tol)    */
+  CPD_STOP_MAXITER = 8
+} cpd_stop_reason;
+
+/* Initialisation (Sec. 4.1.2). */
+typedef enum {
+  CPD_INIT_MLSVD = 0,   /* R core entries of largest |s| as rank-one terms          */
+  CPD_INIT_RANDOM = 1,  /* N(0,1) by Box-Muller on SplitMix64 stream 2 of `seed`    */
+  CPD_INIT_GIVEN = 2    /* caller's W0 in the ORIGINAL space (projected under compression) */
+} cpd_init;
+
+/* Arithmetic of the compression Gram matrices. */
+typedef enum {
+  CPD_GRAM_FP32 = 0,    /* FP32 CUDA-core Gram                                   */
+  CPD_GRAM_BF16 = 1     /* BF16 tcgen05 tensor-core Gram, FP32 accumulate (mode 1);
+                           accuracy is won back by refinement in the original space */
+} cpd_gram_precision;
+
+/* Element type of the input tensor. */
+typedef enum { CPD_F32 = 0, CPD_F64 = 1 } cpd_dtype;
+
+/* Options; cpd_default_options() fills the thesis's defaults. */
+typedef struct {
+  int maxiter;          /* 200: dGN iteration cap (Sec. 4.1.3 "Main parameters")   */
+  double tol;           /* 1e-6: every stop test and the CG test ||r||^2 < tol    */
+  double tau;           /* 1.0: mu0 = tau * mean|S| (Sec. 4.1.3)                  */
+  double cg_a, cg_b;    /* 0.4, 0.9: cg_maxiter ~ U[1+ceil(k^a), 2+ceil(k^b)] (Sec. 4.1.3, 4.4) */
+  double mlsvd_tol;     /* 1e-6: truncation tolerance (Algorithm "Compression") */
+  int st_mlsvd;         /* 1: sequentially truncated MLSVD; 0: classic MLSVD     */
+  int compress;         /* 1: compress then dGN on the core; 0: dGN on T itself  */
+  int init;             /* cpd_init                                              */
+  int gram_precision;   /* cpd_gram_precision                                    */
+  int refine_maxiter;   /* dGN iterations on T after uncompression (0 = none)   */
+  uint64_t seed;        /* SplitMix64 seed for cg_maxiter (stream 1) and init    */
+  int block_threads;    /* threads of the single-CTA solver kernels (0 = auto)   */
+} cpd_options;
+
+/* Outcome of one CPD. */
+typedef struct {
+  int status;           /* cpd_status of this item                               */
+  int iters;            /* dGN iterations on the core (or on T if compress = 0)  */
+  int stop_reason;      /* cpd_stop_reason of that stage                         */
+  int cg_total;         /* CG iterations of that stage                           */
+  double rel_err;       /* last ||S - S_k|| / ||S|| of that stage                */
+  double mu;            /* damping parameter after the last iteration            */
+  double grad_inf;      /* ||grad F||_inf at the last iterate                    */
+  int core_dims[CPD_MAX_ORDER];  /* truncated multilinear rank (or dims of T)    */
+  int refine_iters;     /* refinement iterations run                             */
+  int refine_stop_reason;
+  int refine_cg_total;
+  double refine_rel_err;  /* ||T - T_k|| / ||T|| after refinement (FP64-accumulated) */
+} cpd_info;
+
+/* Per-iteration trace record (optional, device memory, 8 doubles each):
+ * {k, rel_err, mu, gain_ratio, cg_iterations, ||x||, ||grad F||_inf, stage}
+ * stage 0 = core dGN, 1 = refinement. */
+#define CPD_TRACE_FIELDS 8
+
+void cpd_default_options(cpd_options* opts);
+const char* cpd_status_string(int status);
+
+/* Bytes of workspace cpd_compress / cpd_dgn_solve need for this problem. */
+size_t cpd_workspace_size(int L, const int64_t* dims, int R, const cpd_options* opts);
+
+/*
+ * cpd_compress — truncated MLSVD of T (Algorithm "Compression", Sec. 4.1.1,
+ * on Algorithm "MLSVD" or "ST-MLSVD", Sec. 2.2), through the Gram matrices
+ * T_(l) T_(l)^T and their leading eigenpairs (App. A).
+ *   T           device, FP32, column-major I1 x ... x IL
+ *   U_out       device, FP32: L blocks, block l is I_l x P_l column-major,
+ *               P_l = min(I_l, R); only the first R~_l columns are meaningful
+ *   core_out    device, FP32, prod(P_l) entries: the core, column-major with
+ *               the TRUNCATED dims R~_1 x ... x R~_L packed at the start
+ *   sigma_out   device, FP32, sum(P_l): leading singular values per mode
+ *               (of the sequential unfoldings under ST-MLSVD)
+ *   core_dims_out host, L ints: R~_l (synchronises the stream)
+ * Singular vectors are sign-normalised (largest-|.| entry positive).
+ */
+int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_options* opts,
+                 float* U_out, float* core_out, float* sigma_out, int* core_dims_out,
+                 void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * cpd_dgn_solve — the whole method of Fig. "tensorfox-flow" (Sec. 4.1):
+ * compression (if opts->compress), initialisation, damped Gauss-Newton on the
+ * core (Sec. 4.1.3: residual, MTTKRP gradient, Hadamard-of-Gram Pi matrices,
+ * matrix-free J^T J v of Theorem "Hv" inside Jacobi-preconditioned CG with the
+ * diagonal regulariser of Sec. 4.7), uncompression (Sec. 4.1.4), optional
+ * refinement iterations on T, and output normalisation.
+ *   T          device, element type `dtype` (CPD_F64 only with compress = 0)
+ *   W0         device, FP32, stacked I_l x R blocks (INIT_GIVEN), else NULL
+ *   W_out      device, FP32, stacked I_l x R blocks with unit columns
+ *   lambda_out device, FP32, R weights, descending: T ~ sum_r lambda_r w_r^(1) o ... o w_r^(L)
+ *   info       host (synchronises the stream); may be NULL (no sync)
+ *   trace      device, CPD_TRACE_FIELDS doubles per iteration, capacity
+ *              (maxiter + refine_maxiter) records, or NULL
+ */
+int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
+                  const cpd_options* opts, const float* W0, float* W_out, float* lambda_out,
+                  cpd_info* info, double* trace, void* workspace, size_t ws_bytes,
+                  void* stream);
+
+/*
+ * cpd_batch_solve — B independent third-order CPDs of uneven shapes, each
+ * compressed, solved and uncompressed by one CTA of one persistent launch
+ * that takes items from a device work queue ordered longest-first.
+ *   T_packed   device, FP32: the B tensors back to back, item b at element
+ *              offset t_off[b] (host array, B entries)
+ *   dims       host, B x 3 ints (I1, I2, I3 per item), each in [2, 64]
+ *   ranks      host, B ints in [1, 16]
+ *   W_packed   device, FP32 outputs: item b's stacked factors at element
+ *              offset w_off[b] (host), R_b * (I1+I2+I3) floats
+ *   lam_packed device, FP32 outputs: item b's R_b weights at offset l_off[b]
+ *   infos      host, B records (synchronises the stream) or NULL
+ * The per-item options are `opts` (compress, init MLSVD/RANDOM, tolerances);
+ * item b uses seed opts->seed + b.
+ */
+size_t cpd_batch_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts);
+int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const int* dims,
+                    const int* ranks, const cpd_options* opts, float* W_packed,
+                    const int64_t* w_off, float* lam_packed, const int64_t* l_off,
+                    cpd_info* infos, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- component calls (the same device code the solvers run), for testing
+ *      and for callers that compose the steps themselves ---------------------- */
+
+/*
+ * cpd_core_eval — residual and gradient on a small tensor by one CTA
+ * (Sec. 4.1.3 "Computing the residual" and "Computing the gradient"):
+ *   f = S - [[W]]; fsq = ||f||^2 (FP64 accumulation); g = A^T b = -grad F,
+ *   block l of g = f_(l) (W^(L) ⊙ .. ⊙ W^(l+1) ⊙ W^(l-1) ⊙ .. ⊙ W^(1)).
+ *   S, W device FP32; f_out (prod dims, may be NULL), g_out (stacked blocks)
+ *   device FP32; fsq_out device double[1].
+ */
+int cpd_core_eval(const float* S, int L, const int64_t* dims, int R, const float* W,
+                  float* f_out, float* g_out, double* fsq_out, void* workspace,
+                  size_t ws_bytes, void* stream);
+
+/*
+ * cpd_jtj_apply — out = J^T J v for the CPD W (Theorem "Hv", Sec. 3.3.2):
+ *   block l' of out = V^(l') Pi^(l') + sum_{l''≠l'} W^(l') (Pi^(l',l'') * (V^(l'')^T W^(l''))).
+ *   W, V, out device FP32 stacked blocks.
+ */
+int cpd_jtj_apply(int L, const int64_t* dims, int R, const float* W, const float* V,
+                  float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * cpd_mode_gram — G = T_(l) T_(l)^T (I_l x I_l, FP32, column-major), the Gram
+ * route to the left singular vectors of the unfolding (App. A).  precision is
+ * a cpd_gram_precision (BF16 supported for mode l = 0 only).
+ */
+int cpd_mode_gram(const float* T, int L, const int64_t* dims, int mode, int precision,
+                  float* G_out, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * cpd_refine_eval — one pass over a large tensor T (FP32): residual
+ * e = T - [[W]], esq = ||e||^2 (FP64 accumulation, device double[1]) and the
+ * MTTKRP of e for every mode into g_out (stacked blocks, = -grad F).
+ */
+int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const float* W,
+                    float* g_out, double* esq_out, void* workspace, size_t ws_bytes,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPD_H_ */

@@ -1,0 +1,257 @@
+// Single-CTA damped Gauss-Newton on a small tensor (the compressed core, or T
+// itself when no compression is asked for): Sec. 4.1.3 of the thesis, all
+// iterations in one launch, no host round trip.  Also the component kernels
+// behind cpd_core_eval and cpd_jtj_apply, which run the same device code.
+#include "kernels.h"
+#include "solver.cuh"
+
+namespace cpdk {
+
+__host__ __device__ size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem) {
+  Shape s; make_shape(s, L, d, R);
+  const size_t RR = (size_t)R * R;
+  size_t f = 0;
+  auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };   // 16-byte granules
+  f += up(L * RR) + up((size_t)L * L * RR) + 2 * up(L * RR) + 3 * up((size_t)L * R);
+  f += 7 * up((size_t)s.n);
+  if (big_in_smem) {
+    const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
+    f += 2 * up((size_t)s.N) + up(R * NL) + up(R * N0);
+  }
+  return 128 * sizeof(double) + f * sizeof(float);
+}
+
+__host__ __device__ size_t dgn_gscratch_floats(int L, const int* d, int R) {
+  Shape s; make_shape(s, L, d, R);
+  const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
+  auto up = [](size_t x) { return (x + 63) & ~(size_t)63; };
+  return 2 * up((size_t)s.N) + up(R * NL) + up(R * N0);
+}
+
+// Carve the solver's buffers: small ones always in shared memory, tensor-sized
+// ones in shared memory when big_in_smem, else in the global scratch.
+__device__ void carve(const Shape& s, Bufs& b, unsigned char* smem, float* gscratch,
+                      int big_in_smem, float** Sbuf) {
+  const int L = s.L, R = s.R;
+  const size_t RR = (size_t)R * R;
+  auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
+  b.red = reinterpret_cast<double*>(smem);
+  float* p = reinterpret_cast<float*>(smem + 128 * sizeof(double));
+  b.gram = p; p += up(L * RR);
+  b.Pi2 = p; p += up((size_t)L * L * RR);
+  b.Xm = p; p += up(L * RR);
+  b.Ym = p; p += up(L * RR);
+  b.msq = p; p += up((size_t)L * R);
+  b.gam = p; p += up((size_t)L * R);
+  b.sc = p; p += up((size_t)L * R);
+  float** vecs[7] = {&b.W, &b.G, &b.X, &b.Rr, &b.P, &b.Z, &b.Tmp};
+  for (int v = 0; v < 7; ++v) { *vecs[v] = p; p += up((size_t)s.n); }
+  const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
+  float* q = p;
+  size_t a16 = 4;
+  if (!big_in_smem) { q = gscratch; a16 = 64; }
+  auto upg = [a16](size_t x) { return (x + a16 - 1) & ~(a16 - 1); };
+  *Sbuf = q; q += upg((size_t)s.N);
+  b.F = q; q += upg((size_t)s.N);
+  b.Kb = q; q += upg(R * NL);
+  b.Bb = q; q += upg(R * N0);
+  b.S = *Sbuf;
+}
+
+// Load the tensor into the solver's buffer (FP64 input is rounded to FP32),
+// and return ||S|| and mean|S| (FP64 accumulation).
+__device__ void load_tensor(const Shape& s, const void* src, int f64, float* dst, double* red,
+                            double& norm, double& meanabs) {
+  double v[2] = {0.0, 0.0};
+  for (int e = threadIdx.x; e < s.N; e += blockDim.x) {
+    const float x = f64 ? (float)static_cast<const double*>(src)[e] : static_cast<const float*>(src)[e];
+    dst[e] = x;
+    v[0] += (double)x * (double)x;
+    v[1] += fabs((double)x);
+  }
+  block_sum<2>(v, red);
+  norm = sqrt(v[0]);
+  meanabs = v[1] / (double)s.N;
+}
+
+// Initialisation (Sec. 4.1.2).  MLSVD-energy: the R entries of largest |s|
+// (ties to the smaller column-major index) as rank-one terms s e_j1 o ... o e_jL,
+// s on mode 1.  Random: N(0,1) by Box-Muller on SplitMix64.  Given: copy.
+template <int L>
+__device__ void init_factors(const Shape& s, const Bufs& b, int mode, const float* W0,
+                             uint64_t seed, int* chosen) {
+  const int R = s.R;
+  if (mode == CPD_INIT_GIVEN) {
+    for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = W0[j];
+  } else if (mode == CPD_INIT_RANDOM) {
+    for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = (float)normal_draw(seed, (uint64_t)j);
+  } else {
+    for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = 0.f;
+    const int take = R < s.N ? R : s.N;
+    for (int r = 0; r < take; ++r) {
+      float best = -1.f; int bi = 0x7fffffff;
+      for (int e = threadIdx.x; e < s.N; e += blockDim.x) {
+        bool used = false;
+        for (int t = 0; t < r; ++t) used |= (chosen[t] == e);
+        const float v = fabsf(b.S[e]);
+        if (!used && (v > best || (v == best && e < bi))) { best = v; bi = e; }
+      }
+      block_argmax(best, bi, b.red);
+      if (threadIdx.x == 0) chosen[r] = bi;
+      __syncthreads();
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      int e = chosen[r % take];
+      const float val = b.S[e];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const int il = e % s.d[l]; e /= s.d[l];
+        b.W[s.off[l] + r * s.d[l] + il] = (l == 0) ? val : 1.f;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_dgn_core(DgnArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ State st;
+  __shared__ int chosen[kMaxR];
+  int dims[kMaxL];
+  for (int l = 0; l < kMaxL; ++l) dims[l] = (l < L) ? (a.dev_dims ? a.dev_dims[l] : a.dims[l]) : 1;
+  Shape s; make_shape(s, L, dims, a.R);
+  Bufs b; float* Sbuf;
+  carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf);
+
+  double normS, meanabs;
+  load_tensor(s, a.S, a.s_f64, Sbuf, b.red, normS, meanabs);
+  init_factors<L>(s, b, a.init, a.W0, a.seed, chosen);
+  balance<L>(s, b);
+  double fsq, ginf;
+  core_pass<L>(s, b, fsq, ginf);
+  if (threadIdx.x == 0) {
+    st.mu = a.mu0 >= 0.0 ? a.mu0 : a.tau * meanabs;
+    st.F = 0.5 * fsq;
+    st.normS = normS;
+    st.rel_err = normS > 0.0 ? sqrt(fsq) / normS : 0.0;
+    st.grad_inf = ginf;
+    st.kglob = a.k0; st.cg_total = 0; st.stop = 0; st.iters = 0;
+    st.status = isfinite(fsq) ? CPD_OK : CPD_ERR_NUMERIC;
+    if (st.status != CPD_OK) st.stop = CPD_STOP_NONE;
+    a.hist[0] = st.rel_err;
+  }
+  __syncthreads();
+  const bool bad0 = st.status != CPD_OK;
+  for (int k = 1; k <= a.maxiter && !bad0; ++k) {
+    const double mu = st.mu;
+    grams_pi<L>(s, b);
+    regularize<L>(s, b, mu);
+    const int maxit = cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
+    const int its = pcg<L>(s, b, mu, maxit, a.tol);
+    double pred_drop, step;
+    finish_step<L>(s, b, pred_drop, step);
+    core_pass<L>(s, b, fsq, ginf);
+    if (threadIdx.x == 0) {
+      double m = st.mu;
+      const double Fn = 0.5 * fsq;
+      const double gain = gain_update(st.F, Fn, pred_drop, m);
+      const double e = st.normS > 0.0 ? sqrt(fsq) / st.normS : 0.0;
+      st.mu = m; st.F = Fn; st.rel_err = e; st.grad_inf = ginf;
+      st.cg_total += its; st.iters = k; st.kglob = a.k0 + k;
+      a.hist[k] = e;
+      write_trace(a.trace, a.trace_cap, a.trace_slot0 + k - 1, a.k0 + k, e, m, gain, its, step,
+                  ginf, 0);
+      if (!isfinite(fsq) || !isfinite(step)) { st.status = CPD_ERR_NUMERIC; st.stop = CPD_STOP_NONE; }
+      else st.stop = stop_test(k, a.maxiter, a.tol, e, step, ginf, st.normS, a.hist);
+    }
+    __syncthreads();
+    if (st.stop != CPD_STOP_NONE || st.status != CPD_OK) break;
+  }
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) a.W_out[j] = b.W[j];
+  if (threadIdx.x == 0) {
+    DevResult* r = a.res;
+    r->status = st.status; r->iters = st.iters; r->stop = st.stop; r->cg_total = st.cg_total;
+    r->kglob = st.kglob; r->rel_err = st.rel_err; r->mu = st.mu; r->grad_inf = st.grad_inf;
+    r->normS = st.normS;
+  }
+}
+
+// cpd_core_eval: one residual + gradient pass by the solver's own code.
+template <int L>
+__global__ void __launch_bounds__(1024) k_core_eval(CoreEvalArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shape s; make_shape(s, L, a.dims, a.R);
+  Bufs b; float* Sbuf;
+  carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf);
+  double nrm, meanabs;
+  load_tensor(s, a.S, 0, Sbuf, b.red, nrm, meanabs);
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = a.W[j];
+  __syncthreads();
+  double fsq, ginf;
+  core_pass<L>(s, b, fsq, ginf);
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) a.g_out[j] = b.G[j];
+  if (a.f_out)
+    for (int e = threadIdx.x; e < s.N; e += blockDim.x) a.f_out[e] = b.F[e];
+  if (threadIdx.x == 0) *a.fsq_out = fsq;
+}
+
+// cpd_jtj_apply: Grams, Pi matrices and Theorem "Hv" by the solver's own code.
+template <int L>
+__global__ void __launch_bounds__(1024) k_jtj_apply(JtjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shape s; make_shape(s, L, a.dims, a.R);
+  Bufs b; float* Sbuf;
+  carve(s, b, smem_raw, nullptr, 0, &Sbuf);   // no tensor-sized buffers used
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) { b.W[j] = a.W[j]; b.Tmp[j] = a.V[j]; }
+  __syncthreads();
+  grams_pi<L>(s, b);
+  hv_xy<L>(s, b, b.Tmp);
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    a.out[j] = hv_entry<L>(s, b, b.Tmp, l, i, r);
+  }
+}
+
+size_t jtj_smem_bytes(int L, const int* d, int R) {
+  Shape s; make_shape(s, L, d, R);
+  int dd[kMaxL] = {1, 1, 1, 1};
+  for (int l = 0; l < L; ++l) dd[l] = d[l];
+  (void)s;
+  return dgn_smem_bytes(L, dd, R, 0);
+}
+
+template <int L>
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st) {
+  const void* fn = (L == 3) ? (const void*)k_dgn_core<3> : (const void*)k_dgn_core<4>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L == 3) k_dgn_core<3><<<1, threads, smem, st>>>(a);
+  else k_dgn_core<4><<<1, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core_eval(int L, const CoreEvalArgs& a, int threads, size_t smem, cudaStream_t st) {
+  const void* fn = (L == 3) ? (const void*)k_core_eval<3> : (const void*)k_core_eval<4>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L == 3) k_core_eval<3><<<1, threads, smem, st>>>(a);
+  else k_core_eval<4><<<1, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jtj_apply(int L, const JtjArgs& a, int threads, size_t smem, cudaStream_t st) {
+  const void* fn = (L == 3) ? (const void*)k_jtj_apply<3> : (const void*)k_jtj_apply<4>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L == 3) k_jtj_apply<3><<<1, threads, smem, st>>>(a);
+  else k_jtj_apply<4><<<1, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cpdk

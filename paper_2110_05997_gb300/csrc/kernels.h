@@ -1,0 +1,179 @@
+// Argument blocks and host-side launchers of the CPD kernels (internal header
+// shared by the translation units of libcpd).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/cpd.h"
+
+namespace cpdk {
+
+struct DevResult;
+
+struct Dims4 { long long v[CPD_MAX_ORDER]; };
+
+// Single-CTA dGN on an in-CTA tensor (k_dgn.cu).
+struct DgnArgs {
+  int R;
+  int dims[CPD_MAX_ORDER];
+  const int* dev_dims;        // core dims decided on the device, or nullptr
+  const void* S;              // tensor (global), FP32 or FP64
+  int s_f64;
+  const float* W0;            // INIT_GIVEN factors (core space) or nullptr
+  int init;
+  uint64_t seed;
+  double tol, tau, cg_a, cg_b;
+  int maxiter;
+  double mu0;                 // < 0: tau * mean|S|
+  int k0;                     // global iteration offset for cg_maxiter
+  int big_in_smem;
+  float* gscratch;            // tensor-sized buffers when not in shared memory
+  double* hist;               // maxiter + 1 doubles
+  double* trace;              // CPD_TRACE_FIELDS doubles per record, or nullptr
+  int trace_cap, trace_slot0;
+  float* W_out;               // balanced factors, stacked blocks
+  DevResult* res;
+};
+
+struct CoreEvalArgs {
+  int R;
+  int dims[CPD_MAX_ORDER];
+  const float* S;
+  const float* W;
+  float* f_out;
+  float* g_out;
+  double* fsq_out;
+  int big_in_smem;
+  float* gscratch;
+};
+
+struct JtjArgs {
+  int R;
+  int dims[CPD_MAX_ORDER];
+  const float* W;
+  const float* V;
+  float* out;
+};
+
+__host__ __device__ size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem);
+__host__ __device__ size_t dgn_gscratch_floats(int L, const int* d, int R);
+
+cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_core_eval(int L, const CoreEvalArgs& a, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_jtj_apply(int L, const JtjArgs& a, int threads, size_t smem, cudaStream_t st);
+
+// ---- compression (k_compress.cu) ---------------------------------------------
+// A tensor viewed as (a, b, c) around mode l: a = prod_{j<l} dims, b = dims[l],
+// c = prod_{j>l} dims.  Under ST-MLSVD, `a` depends on truncation ranks decided
+// on the device: a = a_host * prod(dev_ranks[0..nr-1]) when dev_ranks != nullptr.
+struct View3 {
+  long long a_host, b, c;
+  const int* dev_ranks;       // ranks of the modes before l (device), or nullptr
+  int nr;
+};
+
+cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G, cudaStream_t st);
+cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float* G, float* scratch,
+                                size_t scratch_bytes, cudaStream_t st);
+size_t gram_bf16_tc_scratch_bytes(long long I, long long C);
+struct EigArgs {
+  const float* G;             // I x I
+  int I, P;                   // P = min(I, R) leading eigenpairs
+  float* U;                   // I x P, column-major
+  float* sigma;               // P
+  int* rank_out;              // device: truncation rank of this mode
+  double mlsvd_tol;
+  int L;
+  uint64_t seed;
+  float* work;                // global scratch when G does not fit shared memory
+};
+cudaError_t launch_eig(const EigArgs& a, cudaStream_t st);
+size_t eig_work_floats(int I, int P);
+// Y(a, r, c) = sum_j U[j, r] T(a, j, c), r < rank (device) <= rmax.
+cudaError_t launch_project(const float* T, View3 v, long long a_max, const float* U,
+                           const int* dev_rank, int rmax, float* Y, cudaStream_t st);
+// Pack the truncated core (dims from the device) from a buffer laid out with
+// the same truncated dims: a copy (kept separate for clarity of ownership).
+cudaError_t launch_copy_f32(const float* src, float* dst, long long n, cudaStream_t st);
+
+// ---- uncompression, refinement, output (k_refine.cu) -----------------------------
+struct PlanDims {                 // device-side dims of the current problem
+  int core[CPD_MAX_ORDER];
+};
+cudaError_t launch_uncompress(int L, const long long* dims, int R, const float* U, const int* core_dims,
+                              const int* Pdims, const float* Wc, float* Wfull, cudaStream_t st);
+cudaError_t launch_project_given(int L, const long long* dims, int R, const float* U,
+                                 const int* core_dims, const int* Pdims, const float* W0,
+                                 float* Wc, cudaStream_t st);
+cudaError_t launch_normalize(int L, const long long* dims, int R, const float* W, float* W_out,
+                             float* lam_out, cudaStream_t st);
+
+struct RefineState;
+struct RefinePassArgs {
+  const float* T;
+  long long dims[CPD_MAX_ORDER];
+  int L, R;
+  const float* W;             // stacked factors (global)
+  float* G;                   // stacked MTTKRP of the residual (zeroed by the launcher)
+  double* esq;                // [0] = ||e||^2, [1] = ||T||^2 (if want_tsq)
+  int want_tsq;
+  const int* done;            // skip when *done != 0 (refinement stopped)
+};
+cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st);
+
+struct RefineStepArgs {
+  int L, R;
+  long long dims[CPD_MAX_ORDER];
+  float* W;                   // global stacked factors (updated in place)
+  const float* G;             // global MTTKRP of the residual at W
+  const double* esq;          // ||e||^2 at W, ||T||^2
+  RefineState* state;         // global
+  float* vecs;                // global scratch for the CG vectors if not in shared memory
+  int vec_in_smem;
+  int j;                      // refinement iteration index (0 = only prime the state)
+  int maxiter;
+  double tol, cg_a, cg_b;
+  uint64_t seed;
+  double* hist;               // maxiter + 1
+  double* trace;
+  int trace_cap, trace_slot0;
+  int* done;
+};
+size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem);
+cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, int* done,
+                               cudaStream_t st);
+size_t refine_state_bytes();
+cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, int* cg_total,
+                               double* rel_err, double* mu, int* status, cudaStream_t st);
+
+// ---- batched (k_batch.cu) ----------------------------------------------------------
+struct BatchItem {
+  long long t_off, w_off, l_off;
+  int d[3];
+  int R;
+};
+struct BatchArgs {
+  const float* T;
+  float* W;
+  float* lam;
+  const BatchItem* items;     // device, sorted longest-first
+  int B;
+  int* queue;                 // device work counter (zeroed by the launcher)
+  cpd_info* infos;            // device
+  float* scratch;             // per-CTA scratch
+  size_t scratch_floats_per_cta;
+  double* hist;               // per-CTA history, maxiter + 1 each
+  int maxiter;
+  double tol, tau, cg_a, cg_b, mlsvd_tol;
+  int compress, init;
+  uint64_t seed;
+  int ctas;
+};
+size_t batch_smem_bytes(int dmax, int Rmax);
+size_t batch_scratch_floats(int dmax, int Rmax);
+cudaError_t launch_batch(const BatchArgs& a, int threads, size_t smem, cudaStream_t st);
+
+}  // namespace cpdk

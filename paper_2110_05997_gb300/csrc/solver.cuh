@@ -1,0 +1,405 @@
+// CTA-level damped Gauss-Newton building blocks (thesis Sec. 3.3, 4.1.3, 4.7).
+//
+// Every function here is executed by ALL threads of one CTA; vectors of the
+// parameter space (length n = R * sum I_l, stacked vec blocks of Sec. 3.1)
+// live in shared memory (or in global memory when they do not fit), R x R
+// matrices always in shared memory.  FP32 data, FP64 scalars (CG alpha/beta,
+// ||r||^2, F, mu, gain ratio) as the precision contract asks.
+#pragma once
+
+#include "common.cuh"
+
+namespace cpdk {
+
+struct Shape {
+  int L, R, n, N;
+  int d[kMaxL];
+  int off[kMaxL + 1];   // start of block l in the stacked vector; off[L] = n
+};
+
+__host__ __device__ inline void make_shape(Shape& s, int L, const int* d, int R) {
+  s.L = L; s.R = R; s.N = 1; s.off[0] = 0;
+  for (int l = 0; l < kMaxL; ++l) s.d[l] = 1;
+  for (int l = 0; l < L; ++l) { s.d[l] = d[l]; s.N *= d[l]; s.off[l + 1] = s.off[l] + R * d[l]; }
+  s.n = s.off[L];
+}
+
+// Working buffers of the solver.  Pi2 holds Pi^(a,b) for a != b and, on its
+// diagonal blocks (a, a), Pi^(a) (the same Hadamard product over j != a).
+struct Bufs {
+  const float* S;  float* F;  float* Kb;  float* Bb;          // tensor-sized (core pass)
+  float* W; float* G; float* X; float* Rr; float* P; float* Z; float* Tmp;  // n each
+  float* gram; float* Pi2; float* Xm; float* Ym;              // L*R*R, L*L*R*R, L*R*R, L*R*R
+  float* msq; float* gam; float* sc;                          // L*R each
+  double* red;                                                // >= 128 doubles, shared
+};
+
+// Iteration state, kept in shared memory by the single-CTA solvers and in
+// global memory between the kernels of the refinement loop.
+struct State {
+  double mu, F, normS, pred_drop, step, grad_inf, rel_err;
+  int k, kglob, cg_total, stop, status, iters;
+};
+
+struct DevResult {
+  int status, iters, stop, cg_total, kglob, pad0;
+  double rel_err, mu, grad_inf, normS;
+};
+
+template <int L>
+__device__ __forceinline__ void decode_j(const Shape& s, int j, int& l, int& i, int& r) {
+  l = 0;
+#pragma unroll
+  for (int t = 1; t < L; ++t) l += (j >= s.off[t]) ? 1 : 0;
+  const int q = j - s.off[l];
+  r = q / s.d[l];
+  i = q - r * s.d[l];
+}
+
+// pi^(l) = W^(l)T W^(l) and the Pi matrices as Hadamard products of the
+// other modes' Grams (Sec. 3.3.2, the display defining Pi^(l',l'') and Pi^(l')).
+template <int L>
+__device__ void grams_pi(const Shape& s, const Bufs& b) {
+  const int R = s.R, RR = R * R;
+  for (int q = threadIdx.x; q < L * RR; q += blockDim.x) {
+    const int l = q / RR, rs = q - l * RR, r = rs / R, c = rs - r * R;
+    if (c < r) continue;
+    const float* wr = b.W + s.off[l] + r * s.d[l];
+    const float* wc = b.W + s.off[l] + c * s.d[l];
+    float acc = 0.f;
+    for (int i = 0; i < s.d[l]; ++i) acc = fmaf(wr[i], wc[i], acc);
+    b.gram[l * RR + r * R + c] = acc;
+    b.gram[l * RR + c * R + r] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * L * RR; q += blockDim.x) {
+    const int ab = q / RR, rs = q - ab * RR, a = ab / L, bb = ab - a * L;
+    float p = 1.f;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (j != a && j != bb) p *= b.gram[j * RR + rs];
+    b.Pi2[q] = p;
+  }
+  __syncthreads();
+}
+
+// Diagonal regulariser D (gamma) and Jacobi preconditioner M of Sec. 4.7:
+// gamma_r^(l) = prod_{j!=l}||w_r^(j)|| * max_m max_r' prod_{j!=m}||w_r'^(j)||,
+// M_(l,r) = prod_{j!=l}||w_r^(j)||^2 + mu * gamma_r^(l); msq = M^{-1/2}.
+template <int L>
+__device__ void regularize(const Shape& s, const Bufs& b, double mu) {
+  const int R = s.R, RR = R * R;
+  double mx = 0.0;
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    double p = 1.0;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (j != l) p *= sqrt(fmax((double)b.gram[j * RR + r * R + r], 0.0));
+    b.gam[q] = (float)p;
+    mx = fmax(mx, p);
+  }
+  const double gmax = block_max(mx, b.red);
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    const double g = (double)b.gam[q] * gmax;
+    const double a = (double)b.Pi2[(l * L + l) * RR + r * R + r];
+    b.gam[q] = (float)g;
+    const double m = a + mu * g;
+    b.msq[q] = (float)(m > 0.0 ? 1.0 / sqrt(m) : 1.0);
+  }
+  __syncthreads();
+}
+
+// First two phases of Theorem "Hv": Xm^(l) = V^(l)T W^(l) and
+// Ym^(l') = sum_{l''!=l'} Pi^(l',l'') * Xm^(l'').
+template <int L>
+__device__ void hv_xy(const Shape& s, const Bufs& b, const float* V) {
+  const int R = s.R, RR = R * R;
+  for (int q = threadIdx.x; q < L * RR; q += blockDim.x) {
+    const int l = q / RR, rs = q - l * RR, t = rs / R, r = rs - t * R;
+    const float* vt = V + s.off[l] + t * s.d[l];
+    const float* wr = b.W + s.off[l] + r * s.d[l];
+    float acc = 0.f;
+    for (int i = 0; i < s.d[l]; ++i) acc = fmaf(vt[i], wr[i], acc);
+    b.Xm[q] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * RR; q += blockDim.x) {
+    const int a = q / RR, rs = q - a * RR;
+    float y = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < L; ++bb)
+      if (bb != a) y = fmaf(b.Pi2[(a * L + bb) * RR + rs], b.Xm[bb * RR + rs], y);
+    b.Ym[q] = y;
+  }
+  __syncthreads();
+}
+
+// Last phase of Theorem "Hv" for entry (l, i, r):
+// (V^(l) Pi^(l) + W^(l) Ym^(l))[i, r].
+template <int L>
+__device__ __forceinline__ float hv_entry(const Shape& s, const Bufs& b, const float* V,
+                                          int l, int i, int r) {
+  const int R = s.R, RR = R * R;
+  const float* P1 = b.Pi2 + (l * L + l) * RR;
+  const float* Y = b.Ym + l * RR;
+  const float* Vl = V + s.off[l] + i;
+  const float* Wl = b.W + s.off[l] + i;
+  const int d = s.d[l];
+  float z = 0.f;
+  for (int t = 0; t < R; ++t) {
+    z = fmaf(Vl[t * d], P1[t * R + r], z);
+    z = fmaf(Wl[t * d], Y[t * R + r], z);
+  }
+  return z;
+}
+
+// Algorithm "Conjugate gradient - dGN" (Sec. 4.1.3) on
+// B = M^{-1/2}(J^T J + mu D)M^{-1/2}, x0 = 0, r0 = M^{-1/2} A^T b, stop on
+// ||r||^2 < tol or maxit; x_hat is left in b.X.  Returns the iterations run.
+template <int L>
+__device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const int n = s.n, R = s.R;
+  double v[1] = {0.0};
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    const float m = b.msq[l * R + r];
+    const float rv = m * b.G[j];
+    b.Rr[j] = rv; b.P[j] = rv; b.X[j] = 0.f; b.Tmp[j] = m * rv;
+    v[0] += (double)rv * (double)rv;
+  }
+  block_sum<1>(v, b.red);
+  double rr = v[0];
+  int its = 0;
+  for (int it = 0; it < maxit; ++it) {
+    hv_xy<L>(s, b, b.Tmp);
+    double pz[1] = {0.0};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      int l, i, r; decode_j<L>(s, j, l, i, r);
+      const int q = l * R + r;
+      const float z = b.msq[q] * (hv_entry<L>(s, b, b.Tmp, l, i, r) + (float)mu * b.gam[q] * b.Tmp[j]);
+      b.Z[j] = z;
+      pz[0] += (double)b.P[j] * (double)z;
+    }
+    block_sum<1>(pz, b.red);
+    if (!(pz[0] > 0.0)) break;
+    const double alpha = rr / pz[0];
+    double rn[1] = {0.0};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      b.X[j] = fmaf((float)alpha, b.P[j], b.X[j]);
+      const float rv = fmaf(-(float)alpha, b.Z[j], b.Rr[j]);
+      b.Rr[j] = rv;
+      rn[0] += (double)rv * (double)rv;
+    }
+    block_sum<1>(rn, b.red);
+    const double beta = rr > 0.0 ? rn[0] / rr : 0.0;
+    rr = rn[0];
+    its = it + 1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      int l, i, r; decode_j<L>(s, j, l, i, r);
+      const float pv = fmaf((float)beta, b.P[j], b.Rr[j]);
+      b.P[j] = pv;
+      b.Tmp[j] = b.msq[l * R + r] * pv;
+    }
+    __syncthreads();
+    if (rr < tol) break;
+  }
+  return its;
+}
+
+// Norm-balancing (Sec. 4.1.3 "Updates"): ||w_r^(1)|| = ... = ||w_r^(L)||,
+// common value the geometric mean, signs kept.
+template <int L>
+__device__ void balance(const Shape& s, const Bufs& b) {
+  const int R = s.R;
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    const float* w = b.W + s.off[l] + r * s.d[l];
+    float acc = 0.f;
+    for (int i = 0; i < s.d[l]; ++i) acc = fmaf(w[i], w[i], acc);
+    b.sc[q] = sqrtf(acc);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    double lg = 0.0; bool ok = true;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      const double nj = (double)b.sc[j * R + r];
+      ok = ok && (nj > 0.0);
+      lg += ok ? log(nj) : 0.0;
+    }
+    b.gam[q] = ok ? (float)(exp(lg / L) / (double)b.sc[q]) : 1.f;   // gam reused as scratch
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    b.W[j] *= b.gam[l * R + r];
+  }
+  __syncthreads();
+}
+
+// After the PCG: x = M^{-1/2} x_hat (into b.X), the predicted decrease
+// F - ½||f + Jx||^2 = <g, x> - ½<x, J^T J x> (g = A^T b), the step norm, then
+// w += x and balancing.
+template <int L>
+__device__ void finish_step(const Shape& s, const Bufs& b, double& pred_drop, double& step) {
+  const int R = s.R;
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    b.X[j] *= b.msq[l * R + r];
+  }
+  __syncthreads();
+  hv_xy<L>(s, b, b.X);
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    const double x = (double)b.X[j];
+    v[0] += (double)b.G[j] * x;
+    v[1] += x * (double)hv_entry<L>(s, b, b.X, l, i, r);
+    v[2] += x * x;
+  }
+  block_sum<3>(v, b.red);
+  pred_drop = v[0] - 0.5 * v[1];
+  step = sqrt(v[2]);
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] += b.X[j];
+  __syncthreads();
+  balance<L>(s, b);
+}
+
+// Residual and gradient of a tensor held by the CTA (Sec. 4.1.3 "Computing the
+// residual", "Computing the gradient"): f = S - [[W]], fsq = ||f||^2 in FP64,
+// G = A^T b = -grad F, blockwise f_(l) (Khatri-Rao of the other factors).
+// The MTTKRPs share two contractions of f: over the last mode (serving modes
+// 1..L-1) and over the first mode (serving mode L).
+template <int L>
+__device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& ginf) {
+  const int R = s.R, N = s.N;
+  const int dl = s.d[L - 1], NL = N / dl, d0 = s.d[0], N0 = N / d0;
+  const float* WL = b.W + s.off[L - 1];
+  // K[r][e'] = prod_{j<L-1} W_j[i_j, r] over the first L-1 modes
+  for (int q = threadIdx.x; q < NL; q += blockDim.x) {
+    int idx[kMaxL];
+    int rem = q;
+#pragma unroll
+    for (int j = 0; j < L - 1; ++j) { idx[j] = rem % s.d[j]; rem /= s.d[j]; }
+    for (int r = 0; r < R; ++r) {
+      float p = 1.f;
+#pragma unroll
+      for (int j = 0; j < L - 1; ++j) p *= b.W[s.off[j] + r * s.d[j] + idx[j]];
+      b.Kb[r * NL + q] = p;
+    }
+  }
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int iL = e / NL, q = e - iL * NL;
+    float t = 0.f;
+    for (int r = 0; r < R; ++r) t = fmaf(b.Kb[r * NL + q], WL[r * dl + iL], t);
+    const float f = b.S[e] - t;
+    b.F[e] = f;
+    acc[0] += (double)f * (double)f;
+  }
+  block_sum<1>(acc, b.red);
+  fsq = acc[0];
+  // A[r][e'] = sum_{iL} f[e', iL] W_L[iL, r];  B[r][e''] = sum_{i0} f[i0, e''] W_0[i0, r]
+  for (int q = threadIdx.x; q < R * NL; q += blockDim.x) {
+    const int r = q / NL, e = q - r * NL;
+    const float* w = WL + r * dl;
+    float a = 0.f;
+    for (int iL = 0; iL < dl; ++iL) a = fmaf(b.F[e + NL * iL], w[iL], a);
+    b.Kb[q] = a;
+  }
+  for (int q = threadIdx.x; q < R * N0; q += blockDim.x) {
+    const int r = q / N0, e = q - r * N0;
+    const float* w = b.W + r * d0;
+    const float* f = b.F + d0 * e;
+    float a = 0.f;
+    for (int i0 = 0; i0 < d0; ++i0) a = fmaf(f[i0], w[i0], a);
+    b.Bb[q] = a;
+  }
+  __syncthreads();
+  double gm = 0.0;
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    // source buffer, its strides per mode, and the free modes to sum over
+    const float* src;
+    int base, fm[2], fstride[2], nf = 0;
+    if (l < L - 1) {
+      src = b.Kb + r * NL;
+      int st = 1; base = 0;
+#pragma unroll
+      for (int t = 0; t < L - 1; ++t) {
+        if (t == l) base = i * st; else { fm[nf] = t; fstride[nf] = st; ++nf; }
+        st *= s.d[t];
+      }
+    } else {
+      src = b.Bb + r * N0;
+      int st = 1; base = 0;
+#pragma unroll
+      for (int t = 1; t < L; ++t) {
+        if (t == l) base = i * st; else { fm[nf] = t; fstride[nf] = st; ++nf; }
+        st *= s.d[t];
+      }
+    }
+    float g = 0.f;
+    if (nf == 1) {
+      const float* w = b.W + s.off[fm[0]] + r * s.d[fm[0]];
+      for (int u = 0; u < s.d[fm[0]]; ++u) g = fmaf(src[base + u * fstride[0]], w[u], g);
+    } else {
+      const float* w0 = b.W + s.off[fm[0]] + r * s.d[fm[0]];
+      const float* w1 = b.W + s.off[fm[1]] + r * s.d[fm[1]];
+      for (int u1 = 0; u1 < s.d[fm[1]]; ++u1) {
+        float h = 0.f;
+        const float* sp = src + base + u1 * fstride[1];
+        for (int u0 = 0; u0 < s.d[fm[0]]; ++u0) h = fmaf(sp[u0 * fstride[0]], w0[u0], h);
+        g = fmaf(h, w1[u1], g);
+      }
+    }
+    b.G[j] = g;
+    gm = fmax(gm, (double)fabsf(g));
+  }
+  ginf = block_max(gm, b.red);
+}
+
+// Stop tests of Sec. 4.1.3 in the printed order (reading: windows as printed,
+// checked when k is a multiple of c = 1 + ceil(maxiter/10) and k > 2c).
+// hist[j] = relative error after iteration j (hist[0] the starting point).
+__device__ inline int stop_test(int k, int maxiter, double tol, double e, double step,
+                                double ginf, double normS, const double* hist) {
+  const int c = 1 + (maxiter + 9) / 10;
+  if (e < tol) return CPD_STOP_REL_ERR;
+  if (step < tol) return CPD_STOP_STEP;
+  if (fabs(hist[k - 1] - e) < tol) return CPD_STOP_IMPROVEMENT;
+  if (ginf < tol) return CPD_STOP_GRAD;
+  if (k % c == 0 && k > 2 * c) {
+    double a1 = 0.0, a2 = 0.0, imp = 0.0;
+    for (int j = k - 2 * c; j <= k - c; ++j) a1 += hist[j];
+    for (int j = k - c; j <= k; ++j) { a2 += hist[j]; imp += fabs(hist[j - 1] - hist[j]); }
+    a1 /= c; a2 /= c; imp /= c;
+    if (a1 - a2 < tol) return CPD_STOP_AVG_ERR;
+    if (imp < 1e-3 * a2) return CPD_STOP_AVG_IMPROVEMENT;
+  }
+  if (e > fmax(1.0, normS * normS) / (1e-16 + tol)) return CPD_STOP_DIVERGENCE;
+  if (k == maxiter) return CPD_STOP_MAXITER;
+  return CPD_STOP_NONE;
+}
+
+// Gain ratio (Sec. 3.3.1 / 4.1.3) and the damping update x3 below 0.25,
+// /3 above 0.75 (the rule Sec. 4.1.3 settles on).
+__device__ inline double gain_update(double F_old, double F_new, double pred_drop, double& mu) {
+  const double g = pred_drop > 0.0 ? (F_old - F_new) / pred_drop : 0.0;
+  if (g < 0.25) mu *= 3.0;
+  else if (g > 0.75) mu /= 3.0;
+  return g;
+}
+
+__device__ inline void write_trace(double* trace, int cap, int slot, int k, double e, double mu,
+                                   double gain, int cg, double step, double ginf, int stage) {
+  if (trace == nullptr || slot < 0 || slot >= cap) return;
+  double* t = trace + (size_t)slot * CPD_TRACE_FIELDS;
+  t[0] = k; t[1] = e; t[2] = mu; t[3] = gain; t[4] = cg; t[5] = step; t[6] = ginf; t[7] = stage;
+}
+
+}  // namespace cpdk
