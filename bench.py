@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of the MLSVD-compressed damped Gauss-Newton CPD on one GB300.
+
+Workload (one step = one whole CPD through the C ABI): a 200x200x200 FP32
+tensor of rank 10 with pairwise factor collinearity 0.5 and relative noise
+1e-4 (synthetic, seeded), compressed by ST-MLSVD to a <= 10x10x10 core, dGN on
+the core from the MLSVD-energy start, uncompression and refinement
+iterations on T, output normalisation.  Metric: CPDs per second, with the
+fit of every result checked against the FP64 oracle's (within 1e-6).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun) give every rank its own CPD (independent problems,
+no collective): weak scaling, value = all ranks' CPDs / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "CPDs/sec to fit err <= 1e-6 vs FP64 oracle"
+UNIT = "CPD/s"
+REFINE_MAXITER = 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                    sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=(statistics.median(mhz) if mhz else None), sm_max_mhz=mx,
+                    reasons=sorted(reasons), samples=len(mhz))
+
+
+def workload():
+    c = synth.c2_compressed()
+    return c["T"], c["R"]
+
+
+def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: dict, clk_mhz):
+    """Roofline entry of a stage: algorithmic bytes or flops per launch over
+    its measured average launch time."""
+    N = int(np.prod(dims))
+    I1 = int(dims[0])
+    sms = 152
+    mhz = clk_mhz or pk["sm_max_mhz"]
+    fp32_peak_tf = sms * 128 * 2 * mhz * 1e6 / 1e12          # FP32 FMA pipes, all SMs
+    if stage == "refine_pass":
+        nbytes = 4.0 * N + 4.0 * 2 * R * sum(dims)              # read T, read W, write G
+        ach = nbytes / (per_launch_ms * 1e-3) / 1e9
+        return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    algorithmic_per_launch=nbytes)
+    if stage in ("gram_fp32", "gram_bf16_tc"):
+        # mode-1 Gram G = T_(1) T_(1)^T: I1^2 * (N / I1) multiply-adds (2 flops each)
+        fl = 2.0 * I1 * N
+        if stage == "gram_bf16_tc":
+            nbytes = 4.0 * N
+            ach = nbytes / (per_launch_ms * 1e-3) / 1e9
+            return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                        algorithmic_per_launch=nbytes, flops=fl)
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, unit="TFLOP/s", frac=ach / fp32_peak_tf,
+                    algorithmic_per_launch=fl)
+    if stage == "dgn_core":
+        # per-iteration flop model of Sec. 4.1.3 ("Overall cost of dGN"), with
+        # the measured iterations and CG iterations, on the core dims
+        cd = [d for d in info["core_dims"] if d > 0]
+        L = len(cd)
+        Nc = float(np.prod(cd))
+        sR = float(sum(cd))
+        it = max(1, info["iters"])
+        cg = info["cg_total"] + it          # one extra J^T J x per iteration (gain ratio)
+        fl = it * ((L * R + L - 1) * Nc + L * R * Nc + R * R * (L + sR) + 3 * R * sR) * 2 \
+            + cg * (9 * R + L * R * R) * sR * 2
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, unit="TFLOP/s", frac=ach / fp32_peak_tf,
+                    algorithmic_per_launch=fl)
+    ach = 0.0
+    return dict(bound="latency", achieved=ach, peak=None, unit="-", frac=None)
+
+
+def cpu_baseline(T, R, ours_W=None, ours_lam=None, budget_s: float = 20.0):
+    """The FP64 oracle, as it stands, on the same tensor: whole CPDs until the
+    budget is spent (at least one)."""
+    import oracle as O
+    T64 = T.astype(np.float64)
+    opts = O.Options(refine_maxiter=REFINE_MAXITER)
+    times, res = [], None
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        res = O.cpd(T64, R, opts)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s or len(times) >= 50:
+            break
+    Wo, lo, io = res
+    out = dict(value=len(times) / sum(times), unit=UNIT, cores=os.cpu_count(), kind="oracle",
+               sample=f"{len(times)} whole CPDs of the 200^3 workload (numpy FP64, default BLAS threads)")
+    if ours_W is not None:
+        fo = O.fit(T64, Wo, lo)
+        fg = O.fit(T64, ours_W, ours_lam)
+        c = O.compare_cpd(ours_W, ours_lam, Wo, lo)
+        out["parity"] = dict(fit_gpu=fg, fit_oracle=fo, abs_diff=abs(fg - fo), ok=abs(fg - fo) <= 1e-6,
+                             factor_rel_err=max(c["mode_err"]), lambda_rel_err=c["lam_err"])
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    T, R = workload()
+    import oracle as O
+    T64 = T.astype(np.float64)
+    opts = O.Options(refine_maxiter=REFINE_MAXITER)
+    for _ in range(args.warmup):
+        O.cpd(T64, R, opts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.cpd(T64, R, opts)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4", global_batch=1,
+                            parallelism="host"),
+                cpu_baseline=dict(kind="oracle", cores=os.cpu_count(), value=v, unit=UNIT,
+                                  sample=f"{args.steps} whole CPDs after {args.warmup} warm-up"),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2110_05997_gb300 import build as bld
+    from paper_2110_05997_gb300 import cpd
+
+    bld.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    T, R = workload()
+    dims = T.shape
+    T_flat = synth.flat(T)
+    Td = torch.from_numpy(T_flat).to(dev)
+    opts = cpd.cpd_default_options(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram)
+    ws = torch.empty(cpd.cpd_workspace_size(dims, R, opts), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return cpd.cpd_dgn_solve(Td, dims, R, opts, stream=stream, workspace=ws)
+
+    for _ in range(args.warmup):
+        W, lam, info, _ = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    l0 = cpd.cpd_launch_count()
+    cpd.cpd_profile_enable(True)
+    infos = []
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()                       # evict T (32 MB) from L2 between steps
+            starts[i].record(stream)
+            W, lam, info, _ = step()
+            ends[i].record(stream)
+            infos.append(info)
+        torch.cuda.synchronize()
+    prof = cpd.cpd_profile_read()
+    cpd.cpd_profile_enable(False)
+    launches = cpd.cpd_launch_count() - l0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of T, solve, D2H of W and lambda
+    Th = torch.from_numpy(T_flat).pin_memory()
+    Tdev2 = torch.empty_like(Td)
+    n_out = R * sum(dims)
+    Wh = torch.empty(n_out, dtype=torch.float32).pin_memory()
+    lh = torch.empty(R, dtype=torch.float32).pin_memory()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e0[i].record(stream)
+        Tdev2.copy_(Th, non_blocking=True)
+        W2, lam2, _, _ = cpd.cpd_dgn_solve(Tdev2, dims, R, opts, stream=stream, workspace=ws)
+        Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
+        lh.copy_(lam2, non_blocking=True)
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    e2e = dict(value=world * args.steps / (e2e_ms * 1e-3), unit=UNIT,
+               h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4))
+
+    if rank != 0:
+        return 0
+    pk = peaks()
+    csum = clk.summary()
+    # dominant stage by total device time in the timed region
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    roof = None
+    if dom[0] is not None:
+        per = dom[1]["ms"] / dom[1]["launches"]
+        roof = algorithmic(dom[0], dims, R, infos[-1], per, pk, csum["sm_mhz"])
+        roof.update(kernel=dom[0], launches=dom[1]["launches"], ms_per_launch=per, traffic=None,
+                    peak_source=pk["src"])
+    stages = {k: dict(ms_per_step=v["ms"] / args.steps, launches_per_step=v["launches"] / args.steps)
+              for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4", tensor_dims=list(dims),
+                            rank=R, gram_precision=args.gram, refine_maxiter=REFINE_MAXITER,
+                            global_batch=world, parallelism=f"independent CPD per GPU x{world}",
+                            l2="flushed between steps (256 MB write)"),
+                e2e=e2e, gpu_launches=int(launches), roofline=roof, stages=stages,
+                clocks=csum, solve=dict(core_iters=infos[-1]["iters"], core_stop=infos[-1]["stop_name"],
+                                        core_cg=infos[-1]["cg_total"], core_dims=infos[-1]["core_dims"][:3],
+                                        refine_iters=infos[-1]["refine_iters"],
+                                        refine_rel_err=infos[-1]["refine_rel_err"]))
+    if not args.no_cpu_baseline:
+        Wg = [w.double().cpu().numpy() for w in W]
+        lg = lam.double().cpu().numpy()
+        cb = cpu_baseline(T, R, Wg, lg, budget_s=args.cpu_budget)
+        line["parity"] = cb.pop("parity", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--gram", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

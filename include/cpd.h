@@ -222,6 +222,25 @@ int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const flo
                     float* g_out, double* esq_out, void* workspace, size_t ws_bytes,
                     void* stream);
 
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* Number of kernels this library has launched in this process (all streams). */
+long long cpd_launch_count(void);
+
+/*
+ * Per-stage device timing.  While enabled (on != 0), every launch site of the
+ * solvers records a CUDA event pair on the stream it launches on; stage names
+ * are the launcher names ("gram_fp32", "gram_bf16_tc", "eig", "project",
+ * "dgn_core", "uncompress", "refine_pass", "refine_step", "normalize", ...).
+ * cpd_profile_read synchronises the recorded events, returns up to
+ * max_entries stages (names: 32 chars each, NUL-terminated; ms: total device
+ * milliseconds; launches: launch count) and clears the record.  Returns the
+ * number of stages written, or a negative cpd_status.  Not thread-safe.
+ */
+int cpd_profile_enable(int on);
+int cpd_profile_read(int max_entries, char* names, double* ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ F32, F64 = 0, 1
 
 EXPORTS = ["cpd_default_options", "cpd_status_string", "cpd_workspace_size", "cpd_compress",
            "cpd_dgn_solve", "cpd_batch_workspace_size", "cpd_batch_solve", "cpd_core_eval",
-           "cpd_jtj_apply", "cpd_mode_gram", "cpd_refine_eval"]
+           "cpd_jtj_apply", "cpd_mode_gram", "cpd_refine_eval", "cpd_launch_count",
+           "cpd_profile_enable", "cpd_profile_read"]
 
 
 class CpdError(RuntimeError):
@@ -100,6 +101,12 @@ def lib():
         L.cpd_mode_gram.restype = C.c_int
         L.cpd_refine_eval.argtypes = [vp, C.c_int, i64p, C.c_int, vp, fp, dp, vp, C.c_size_t, vp]
         L.cpd_refine_eval.restype = C.c_int
+        L.cpd_launch_count.argtypes = []
+        L.cpd_launch_count.restype = C.c_longlong
+        L.cpd_profile_enable.argtypes = [C.c_int]
+        L.cpd_profile_enable.restype = C.c_int
+        L.cpd_profile_read.argtypes = [C.c_int, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.cpd_profile_read.restype = C.c_int
         _lib = L
     return _lib
 
@@ -321,3 +328,27 @@ def cpd_batch_solve(T_packed, t_off, dims, ranks, opts: cpd_options | None = Non
                                lof, infos, _ptr(workspace), workspace.numel(), _stream(stream))
     _check("cpd_batch_solve", st)
     return W, lam, w_off, l_off, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def cpd_launch_count() -> int:
+    return int(lib().cpd_launch_count())
+
+
+def cpd_profile_enable(on: bool = True) -> None:
+    _check("cpd_profile_enable", lib().cpd_profile_enable(1 if on else 0))
+
+
+def cpd_profile_read(max_entries: int = 64) -> dict:
+    """Per-stage device milliseconds and launch counts recorded since the last read."""
+    names = C.create_string_buffer(32 * max_entries)
+    ms = (C.c_double * max_entries)()
+    cnt = (C.c_longlong * max_entries)()
+    n = lib().cpd_profile_read(max_entries, names, ms, cnt)
+    if n < 0:
+        raise CpdError("cpd_profile_read", n)
+    raw = names.raw
+    out = {}
+    for i in range(n):
+        nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = dict(ms=float(ms[i]), launches=int(cnt[i]))
+    return out

@@ -158,6 +158,8 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
 }
 
 #define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return CPD_ERR_CUDA; } while (0)
+// launch under a profiling scope on the stream `st` in scope
+#define PL(name, x) do { ProfScope ps_(st, name); CK(x); } while (0)
 
 int fill_dims(SolvePlan& p, int L, const int64_t* dims, int R) {
   p.L = L; p.R = R;
@@ -185,15 +187,15 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       View3 v{1, p.dims[l], c, l > 0 ? p.core_dims_dev : nullptr, l};
       CK(cudaMemsetAsync(p.G, 0, sizeof(float) * (size_t)p.dims[l] * p.dims[l], st));
       if (l == 0 && o.gram_precision == CPD_GRAM_BF16) {
-        CK(launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
+        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
       } else {
-        CK(launch_gram_simt(cur, v, a_max, p.G, st));
+        PL("gram_fp32", launch_gram_simt(cur, v, a_max, p.G, st));
       }
       EigArgs ea{p.G, p.idims[l], p.P[l], p.U + offU, p.sigma + offS, p.core_dims_dev + l,
                  o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work};
-      CK(launch_eig(ea, st));
+      PL("eig", launch_eig(ea, st));
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
-      CK(launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+      PL("project", launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];
@@ -209,12 +211,12 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       View3 v{a, p.dims[l], c, nullptr, 0};
       CK(cudaMemsetAsync(p.G, 0, sizeof(float) * (size_t)p.dims[l] * p.dims[l], st));
       if (l == 0 && o.gram_precision == CPD_GRAM_BF16)
-        CK(launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
+        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
       else
-        CK(launch_gram_simt(T, v, a, p.G, st));
+        PL("gram_fp32", launch_gram_simt(T, v, a, p.G, st));
       EigArgs ea{p.G, p.idims[l], p.P[l], p.U + offU, p.sigma + offS, p.core_dims_dev + l,
                  o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work};
-      CK(launch_eig(ea, st));
+      PL("eig", launch_eig(ea, st));
       offU += (size_t)p.idims[l] * p.P[l];
       offS += p.P[l];
     }
@@ -227,7 +229,7 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       for (int j = l + 1; j < L; ++j) c *= p.dims[j];
       View3 v{1, p.dims[l], c, l > 0 ? p.core_dims_dev : nullptr, l};
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
-      CK(launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+      PL("project", launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];
@@ -321,7 +323,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     a.S = p.core;
     a.s_f64 = 0;
     if (o.init == CPD_INIT_GIVEN) {
-      CK(launch_project_given(L, p.dims, R, p.U, p.core_dims_dev, p.P, W0, p.W0_core, st));
+      PL("project_given", launch_project_given(L, p.dims, R, p.U, p.core_dims_dev, p.P, W0, p.W0_core, st));
       a.W0 = p.W0_core;
     }
   } else {
@@ -337,18 +339,18 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   int cmax[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
   Shape sc; make_shape(sc, L, cmax, R);
-  CK(launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
+  PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
 
   // ---- uncompression, refinement, output ---------------------------------------------
   const float* Wfinal = p.W_core;
   if (o.compress) {
-    CK(launch_uncompress(L, p.dims, R, p.U, p.core_dims_dev, p.P, p.W_core, p.W_full, st));
+    PL("uncompress", launch_uncompress(L, p.dims, R, p.U, p.core_dims_dev, p.P, p.W_core, p.W_full, st));
     Wfinal = p.W_full;
   }
   if (o.refine_maxiter > 0) {
     float* Wr = p.W_full;
     if (!o.compress) CK(cudaMemcpyAsync(Wr, p.W_core, sizeof(float) * p.n_full, cudaMemcpyDeviceToDevice, st));
-    CK(launch_refine_init(p.rstate, p.res, p.rdone, st));
+    PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
     RefinePassArgs pa{};
     pa.T = static_cast<const float*>(T); pa.L = L; pa.R = R; pa.W = Wr; pa.G = p.rG; pa.esq = p.resq;
     for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = p.dims[l];
@@ -362,13 +364,13 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     const int rthreads = 1024;
     for (int j = 0; j <= o.refine_maxiter; ++j) {
       pa.want_tsq = (j == 0);
-      CK(launch_refine_pass(pa, st));
+      PL("refine_pass", launch_refine_pass(pa, st));
       sa.j = j;
-      CK(launch_refine_step(sa, rthreads, p.r_smem, st));
+      PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
     }
     Wfinal = Wr;
   }
-  CK(launch_normalize(L, p.dims, R, Wfinal, W_out, lambda_out, st));
+  PL("normalize", launch_normalize(L, p.dims, R, Wfinal, W_out, lambda_out, st));
 
   if (info) {
     DevResult hr;
@@ -447,7 +449,8 @@ int cpd_core_eval(const float* S, int L, const int64_t* dims, int R, const float
     a.gscratch = static_cast<float*>(workspace);
   }
   Shape s; make_shape(s, L, d, R);
-  CK(launch_core_eval(L, a, 256, sm, as_stream(stream)));
+  cudaStream_t st = as_stream(stream);
+  PL("core_eval", launch_core_eval(L, a, 256, sm, st));
   return CPD_OK;
 }
 
@@ -465,7 +468,8 @@ int cpd_jtj_apply(int L, const int64_t* dims, int R, const float* W, const float
   a.W = W; a.V = V; a.out = out;
   size_t sm = dgn_smem_bytes(L, d, R, 0);
   if (sm > smem_limit()) return CPD_ERR_UNSUPPORTED;
-  CK(launch_jtj_apply(L, a, 256, sm, as_stream(stream)));
+  cudaStream_t st = as_stream(stream);
+  PL("jtj_apply", launch_jtj_apply(L, a, 256, sm, st));
   return CPD_OK;
 }
 
@@ -484,10 +488,10 @@ int cpd_mode_gram(const float* T, int L, const int64_t* dims, int mode, int prec
   if (precision == CPD_GRAM_BF16) {
     size_t need = gram_bf16_tc_scratch_bytes(dims[0], c);
     if (ws_bytes < need || (need > 0 && workspace == nullptr)) return CPD_ERR_WORKSPACE;
-    CK(launch_gram_bf16_tc(T, dims[0], c, G_out, static_cast<float*>(workspace), ws_bytes, st));
+    PL("gram_bf16_tc", launch_gram_bf16_tc(T, dims[0], c, G_out, static_cast<float*>(workspace), ws_bytes, st));
   } else {
     View3 vv{a, dims[mode], c, nullptr, 0};
-    CK(launch_gram_simt(T, vv, a, G_out, st));
+    PL("gram_fp32", launch_gram_simt(T, vv, a, G_out, st));
   }
   return CPD_OK;
 }
@@ -503,7 +507,8 @@ int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const flo
   pa.T = T; pa.L = L; pa.R = R; pa.W = W; pa.G = g_out; pa.esq = esq_out; pa.want_tsq = 1;
   for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = (l < L) ? dims[l] : 1;
   pa.done = nullptr;
-  CK(launch_refine_pass(pa, as_stream(stream)));
+  cudaStream_t st = as_stream(stream);
+  PL("refine_pass", launch_refine_pass(pa, st));
   return CPD_OK;
 }
 

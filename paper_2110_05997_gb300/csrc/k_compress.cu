@@ -86,6 +86,7 @@ cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G,
   long long chunk = (K + splits - 1) / splits;
   chunk = (chunk + kGK - 1) / kGK * kGK;
   k_gram_simt<<<dim3(npair, (unsigned)splits), 256, 0, st>>>(T, v, chunk, ntile, G);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -400,6 +401,7 @@ cudaError_t launch_eig(const EigArgs& a_in, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_eig<<<1, kEigThreads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -481,6 +483,7 @@ cudaError_t launch_project(const float* T, View3 v, long long a_max, const float
       if (blocks > 4 * 152) blocks = 4 * 152;
       if (blocks < 1) blocks = 1;
       k_project_first<<<(unsigned)blocks, 256, smem, st>>>(T, v.b, v.c, U, dev_rank, Y);
+      count_launch();
       return cudaGetLastError();
     }
   }
@@ -489,6 +492,7 @@ cudaError_t launch_project(const float* T, View3 v, long long a_max, const float
   if (blocks > 8 * 152) blocks = 8 * 152;
   if (blocks < 1) blocks = 1;
   k_project_gen<<<(unsigned)blocks, 256, 0, st>>>(T, v, U, dev_rank, Y);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -497,6 +501,7 @@ __global__ void k_copy(const float* s, float* d, long long n) {
 }
 cudaError_t launch_copy_f32(const float* src, float* dst, long long n, cudaStream_t st) {
   k_copy<<<64, 256, 0, st>>>(src, dst, n);
+  count_launch();
   return cudaGetLastError();
 }
 

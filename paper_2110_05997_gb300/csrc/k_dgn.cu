@@ -233,6 +233,7 @@ cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, c
   if (e != cudaSuccess) return e;
   if (L == 3) k_dgn_core<3><<<1, threads, smem, st>>>(a);
   else k_dgn_core<4><<<1, threads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -242,6 +243,7 @@ cudaError_t launch_core_eval(int L, const CoreEvalArgs& a, int threads, size_t s
   if (e != cudaSuccess) return e;
   if (L == 3) k_core_eval<3><<<1, threads, smem, st>>>(a);
   else k_core_eval<4><<<1, threads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -251,6 +253,7 @@ cudaError_t launch_jtj_apply(int L, const JtjArgs& a, int threads, size_t smem, 
   if (e != cudaSuccess) return e;
   if (L == 3) k_jtj_apply<3><<<1, threads, smem, st>>>(a);
   else k_jtj_apply<4><<<1, threads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 

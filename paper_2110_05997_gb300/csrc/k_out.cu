@@ -104,6 +104,7 @@ static Dims4 to_dims4i(int L, const int* d) {
 cudaError_t launch_uncompress(int L, const long long* dims, int R, const float* U, const int* core_dims,
                               const int* Pdims, const float* Wc, float* Wfull, cudaStream_t st) {
   k_uncompress<<<8, 256, 0, st>>>(L, to_dims4(L, dims), R, U, core_dims, to_dims4i(L, Pdims), Wc, Wfull);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -111,12 +112,14 @@ cudaError_t launch_project_given(int L, const long long* dims, int R, const floa
                                  const int* core_dims, const int* Pdims, const float* W0,
                                  float* Wc, cudaStream_t st) {
   k_project_given<<<1, 256, 0, st>>>(L, to_dims4(L, dims), R, U, core_dims, to_dims4i(L, Pdims), W0, Wc);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_normalize(int L, const long long* dims, int R, const float* W, float* W_out,
                              float* lam_out, cudaStream_t st) {
   k_normalize<<<1, 256, 0, st>>>(L, to_dims4(L, dims), R, W, W_out, lam_out);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -169,6 +169,7 @@ cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st) {
   int n = 0;
   for (int l = 0; l < a.L; ++l) n += (int)a.dims[l] * a.R;
   k_zero_pass<<<16, 256, 0, st>>>(a.G, n, a.esq, a.want_tsq, a.done);
+  count_launch();
   const size_t smem = pass_smem(a.L, a.dims, a.R);
   const void* fn = (a.L == 3) ? (const void*)k_refine_pass<3> : (const void*)k_refine_pass<4>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -180,6 +181,7 @@ cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st) {
   if (blocks < 1) blocks = 1;
   if (a.L == 3) k_refine_pass<3><<<(unsigned)blocks, kPassThreads, smem, st>>>(a);
   else k_refine_pass<4><<<(unsigned)blocks, kPassThreads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -274,6 +276,7 @@ cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem
   if (e != cudaSuccess) return e;
   if (a.L == 3) k_refine_step<3><<<1, threads, smem, st>>>(a);
   else k_refine_step<4><<<1, threads, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -286,6 +289,7 @@ __global__ void k_refine_init(RefineState* s, const DevResult* core, int* done) 
 
 cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, int* done, cudaStream_t st) {
   k_refine_init<<<1, 1, 0, st>>>(state, core_res, done);
+  count_launch();
   return cudaGetLastError();
 }
 

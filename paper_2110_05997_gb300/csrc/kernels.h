@@ -14,6 +14,15 @@ struct DevResult;
 
 struct Dims4 { long long v[CPD_MAX_ORDER]; };
 
+// Diagnostics (diag.cu): every kernel launch is counted; while profiling is
+// enabled a ProfScope records a CUDA event pair around its launches.
+void count_launch(int n = 1);
+struct ProfScope {
+  ProfScope(cudaStream_t st, const char* name);
+  ~ProfScope();
+  cudaStream_t st_; const char* name_; cudaEvent_t a_;
+};
+
 // Single-CTA dGN on an in-CTA tensor (k_dgn.cu).
 struct DgnArgs {
   int R;

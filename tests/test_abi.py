@@ -25,7 +25,7 @@ def _declared():
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(cpd_[a-z_0-9]+)\s*\(", src, re.M)
+            names += re.findall(r"^\s*(?:[A-Za-z_][A-Za-z0-9_]*[\s*]+)+(cpd_[a-z_0-9]+)\s*\(", src, re.M)
     return sorted(set(names))
 
 
