@@ -162,6 +162,29 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
                   void* stream);
 
 /*
+ * cpd_dgn_solve_noalloc — cpd_dgn_solve for callers that cannot give the
+ * library a workspace because they may not allocate device memory when they
+ * need a CPD: a plugin inside a framework whose allocator owns all device
+ * memory, or a latency-critical loop where a cudaMalloc (which can synchronise
+ * the device) is not acceptable.  The thesis has no counterpart: this is a
+ * packaging of the uncompressed dGN solve.  It allocates nothing; its scratch
+ * is a 128 KiB array inside the library, held on every GPU that loads the
+ * library until the process exits.
+ * Limits: opts->compress = 0 and opts->refine_maxiter = 0, maxiter <= 4096,
+ * R * (I_1 + ... + I_L) <= 16384, and T must fit the solver CTA's shared
+ * memory; a larger problem returns CPD_ERR_WORKSPACE.  Other arguments and the
+ * results are those of cpd_dgn_solve (no trace).  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and must
+ * come before any stream capture on that device.  Every call uses the same
+ * array and leaves its contents behind: calls whose GPU work can overlap (on
+ * different streams or from different host threads) race and must be
+ * serialised by the caller.
+ */
+int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int64_t* dims, int R,
+                          const cpd_options* opts, const float* W0, float* W_out,
+                          float* lambda_out, cpd_info* info, void* stream);
+
+/*
  * cpd_batch_solve — B independent third-order CPDs of uneven shapes, each
  * compressed, solved and uncompressed by one CTA of one persistent launch
  * that takes items from a device work queue ordered longest-first.

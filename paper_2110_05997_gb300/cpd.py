@@ -31,7 +31,7 @@ F32, F64 = 0, 1
 EXPORTS = ["cpd_default_options", "cpd_status_string", "cpd_workspace_size", "cpd_compress",
            "cpd_dgn_solve", "cpd_batch_workspace_size", "cpd_batch_solve", "cpd_core_eval",
            "cpd_jtj_apply", "cpd_mode_gram", "cpd_refine_eval", "cpd_launch_count",
-           "cpd_profile_enable", "cpd_profile_read"]
+           "cpd_profile_enable", "cpd_profile_read", "cpd_dgn_solve_noalloc"]
 
 
 class CpdError(RuntimeError):
@@ -101,6 +101,8 @@ def lib():
         L.cpd_mode_gram.restype = C.c_int
         L.cpd_refine_eval.argtypes = [vp, C.c_int, i64p, C.c_int, vp, fp, dp, vp, C.c_size_t, vp]
         L.cpd_refine_eval.restype = C.c_int
+        L.cpd_dgn_solve_noalloc.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, optp, vp, fp, fp, infop, vp]
+        L.cpd_dgn_solve_noalloc.restype = C.c_int
         L.cpd_launch_count.argtypes = []
         L.cpd_launch_count.restype = C.c_longlong
         L.cpd_profile_enable.argtypes = [C.c_int]
@@ -352,3 +354,23 @@ def cpd_profile_read(max_entries: int = 64) -> dict:
         nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = dict(ms=float(ms[i]), launches=int(cnt[i]))
     return out
+
+
+def cpd_dgn_solve_noalloc(T_flat, dims, R: int, opts: cpd_options | None = None, W0_flat=None,
+                          stream=None, W_out=None, lam_out=None):
+    """cpd_dgn_solve without a workspace: for callers that may not allocate
+    device memory at solve time.  The library keeps the scratch in a fixed
+    128 KiB device array; the caller still provides (or here, this binding
+    allocates once) the output buffers.  Uncompressed solves only; problems
+    beyond the array's capacity raise CpdError (workspace too small)."""
+    import torch
+    opts = opts or cpd_default_options(compress=0)
+    dtype = F64 if T_flat.dtype == torch.float64 else F32
+    n = R * sum(int(d) for d in dims)
+    W = W_out if W_out is not None else torch.empty(n, dtype=torch.float32, device=T_flat.device)
+    lam = lam_out if lam_out is not None else torch.empty(R, dtype=torch.float32, device=T_flat.device)
+    info = cpd_info()
+    st = lib().cpd_dgn_solve_noalloc(_ptr(T_flat), dtype, len(dims), _dims(dims), int(R), C.byref(opts),
+                                     _ptr(W0_flat), _ptr(W), _ptr(lam), C.byref(info), _stream(stream))
+    _check("cpd_dgn_solve_noalloc", st)
+    return _stacked_split(W, dims, R), lam, info.as_dict()
