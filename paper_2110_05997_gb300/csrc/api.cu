@@ -83,6 +83,7 @@ struct SolvePlan {
   // device buffers
   DevResult* res = nullptr;
   double* hist = nullptr;
+  int* cgtab = nullptr; int cgtab_len = 0;
   float* W_core = nullptr;     // balanced factors after the core dGN (core space)
   float* W_full = nullptr;     // original space (compress path / refinement)
   float* gscratch = nullptr;
@@ -105,6 +106,8 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
   for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
   p.res = c.take<DevResult>(1);
   p.hist = c.take<double>((size_t)o.maxiter + 1);
+  p.cgtab_len = o.maxiter + o.refine_maxiter;
+  p.cgtab = c.take<int>((size_t)p.cgtab_len + 1);
   Shape sc; make_shape(sc, L, cmax, R);
   p.W_core = c.take<float>(sc.n);
   size_t smem_big = dgn_smem_bytes(L, cmax, R, 1);
@@ -302,6 +305,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   if (o.init == CPD_INIT_GIVEN && W0 == nullptr) return CPD_ERR_INVALID_ARG;
   if (dtype == CPD_F64 && (o.compress || o.refine_maxiter > 0)) return CPD_ERR_UNSUPPORTED;
   if (o.gram_precision == CPD_GRAM_BF16 && !o.compress) return CPD_ERR_INVALID_ARG;
+  if (o.refine_maxiter > 0 && !refine_pass_supported((int)dims[0], R)) return CPD_ERR_UNSUPPORTED;
 
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
   Carver c(workspace, ws_bytes);
@@ -336,6 +340,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   a.big_in_smem = p.big_in_smem; a.gscratch = p.gscratch;
   a.hist = p.hist; a.trace = trace; a.trace_cap = trace_cap; a.trace_slot0 = 0;
   a.W_out = p.W_core; a.res = p.res;
+  a.cgtab = p.cgtab; a.cgtab_len = p.cgtab_len;
   int cmax[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
   Shape sc; make_shape(sc, L, cmax, R);
@@ -361,6 +366,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = o.refine_maxiter;
     sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.seed = o.seed; sa.hist = p.rhist;
     sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
+    sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
     const int rthreads = 1024;
     for (int j = 0; j <= o.refine_maxiter; ++j) {
       pa.want_tsq = (j == 0);
@@ -503,6 +509,7 @@ int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const flo
   int v = validate_common(L, dims, R);
   if (v != CPD_OK) return v;
   if (!T || !W || !g_out || !esq_out) return CPD_ERR_INVALID_ARG;
+  if (!refine_pass_supported((int)dims[0], R)) return CPD_ERR_UNSUPPORTED;
   RefinePassArgs pa{};
   pa.T = T; pa.L = L; pa.R = R; pa.W = W; pa.G = g_out; pa.esq = esq_out; pa.want_tsq = 1;
   for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = (l < L) ? dims[l] : 1;

@@ -47,36 +47,64 @@ __device__ inline double normal_draw(uint64_t seed, uint64_t j) {
 }
 
 // ---- block reductions (every thread receives the result) --------------------
-// `red` must hold 32 * NV doubles of shared memory.  Contains two barriers.
+// FP32 partial sums per thread, across the warp (shuffles) and across the
+// warps (every thread adds the <= 32 per-warp partials from shared memory);
+// the result is returned as FP64 for the scalar recurrences.  No FP64
+// instruction is issued: on sm_103a the FP64 pipe runs at ~1/64 of FP32 and
+// a single FP64 add per warp costs more than the whole FP32 reduction.
+// `red` must hold 32 * NV floats (it is declared as doubles by the callers).
+// Contains two barriers.
 template <int NV>
-__device__ inline void block_sum(double (&v)[NV], double* red) {
+__device__ inline void block_sum(const float (&in)[NV], double (&out)[NV], double* red) {
+  float v[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i)
+  for (int i = 0; i < NV; ++i) {
+    v[i] = in[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float* r = reinterpret_cast<float*>(red);
   __syncthreads();
   if (lane == 0)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) red[wid * NV + i] = v[i];
+    for (int i = 0; i < NV; ++i) r[i * 32 + wid] = v[i];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w * NV + i];
-    v[i] = s;
+    float s = lane < nw ? r[i * 32 + lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    out[i] = (double)s;
   }
 }
 
-__device__ inline double block_max(double v, double* red) {
+// a / b and sqrt(x) to ~FP64 accuracy from an FP32 estimate and one FP64
+// correction step (2-3 FP64 FMAs instead of a full FP64 division / square
+// root sequence).  Valid while a, b, x are within the FP32 exponent range.
+__device__ __forceinline__ double quick_div(double a, double b) {
+  const float rb = 1.f / (float)b;
+  const double q0 = (double)((float)a * rb);
+  return fma(fma(-q0, b, a), (double)rb, q0);
+}
+__device__ __forceinline__ double quick_sqrt(double x) {
+  if (!(x > 0.0)) return x == 0.0 ? 0.0 : sqrt(x);
+  const float s0 = sqrtf((float)x);
+  const double s = (double)s0;
+  return fma(fma(-s, s, x), 0.5 / s, s);
+}
+
+__device__ inline float block_max(float v, double* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float* r = reinterpret_cast<float*>(red);
   __syncthreads();
-  if (lane == 0) red[wid] = v;
+  if (lane == 0) r[wid] = v;
   __syncthreads();
-  double m = red[0];
-  for (int w = 1; w < nw; ++w) m = fmax(m, red[w]);
+  float m = lane < nw ? r[lane] : r[0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   return m;
 }
 
@@ -100,5 +128,12 @@ __device__ inline void block_argmax(float& v, int& idx, double* red) {
 }
 
 __device__ inline bool finite_d(double x) { return isfinite(x); }
+
+// a / b (quick_div) computed once per warp (lane 0) and broadcast.
+__device__ __forceinline__ double warp_div(double a, double b) {
+  double q = 0.0;
+  if ((threadIdx.x & 31) == 0) q = quick_div(a, b);
+  return __shfl_sync(0xffffffffu, q, 0);
+}
 
 }  // namespace cpdk

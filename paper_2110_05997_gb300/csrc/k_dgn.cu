@@ -62,14 +62,15 @@ __device__ void carve(const Shape& s, Bufs& b, unsigned char* smem, float* gscra
 // and return ||S|| and mean|S| (FP64 accumulation).
 __device__ void load_tensor(const Shape& s, const void* src, int f64, float* dst, double* red,
                             double& norm, double& meanabs) {
-  double v[2] = {0.0, 0.0};
+  float vf[2] = {0.f, 0.f};
   for (int e = threadIdx.x; e < s.N; e += blockDim.x) {
     const float x = f64 ? (float)static_cast<const double*>(src)[e] : static_cast<const float*>(src)[e];
     dst[e] = x;
-    v[0] += (double)x * (double)x;
-    v[1] += fabs((double)x);
+    vf[0] = fmaf(x, x, vf[0]);
+    vf[1] += fabsf(x);
   }
-  block_sum<2>(v, red);
+  double v[2];
+  block_sum<2>(vf, v, red);
   norm = sqrt(v[0]);
   meanabs = v[1] / (double)s.N;
 }
@@ -119,14 +120,19 @@ __global__ void __launch_bounds__(1024) k_dgn_core(DgnArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ State st;
   __shared__ int chosen[kMaxR];
-  int dims[kMaxL];
-  for (int l = 0; l < kMaxL; ++l) dims[l] = (l < L) ? (a.dev_dims ? a.dev_dims[l] : a.dims[l]) : 1;
-  Shape s; make_shape(s, L, dims, a.R);
+  __shared__ Shape s;       // shared: indexed by runtime mode numbers in every phase
+  if (threadIdx.x == 0) {
+    int dims[kMaxL];
+    for (int l = 0; l < kMaxL; ++l) dims[l] = (l < L) ? (a.dev_dims ? a.dev_dims[l] : a.dims[l]) : 1;
+    make_shape(s, L, dims, a.R);
+  }
+  __syncthreads();
   Bufs b; float* Sbuf;
   carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf);
 
   double normS, meanabs;
   load_tensor(s, a.S, a.s_f64, Sbuf, b.red, normS, meanabs);
+  fill_cg_table(a.cgtab, a.cgtab_len, a.seed, a.cg_a, a.cg_b);
   init_factors<L>(s, b, a.init, a.W0, a.seed, chosen);
   balance<L>(s, b);
   double fsq, ginf;
@@ -142,29 +148,35 @@ __global__ void __launch_bounds__(1024) k_dgn_core(DgnArgs a) {
     if (st.status != CPD_OK) st.stop = CPD_STOP_NONE;
     a.hist[0] = st.rel_err;
   }
+  __shared__ double s_div;
+  if (threadIdx.x == 0) s_div = divergence_threshold(st.normS, a.tol);
   __syncthreads();
   const bool bad0 = st.status != CPD_OK;
+  __shared__ int s_maxit;
   for (int k = 1; k <= a.maxiter && !bad0; ++k) {
     const double mu = st.mu;
-    grams_pi<L>(s, b);
+    if (threadIdx.x == 0)
+      s_maxit = (a.k0 + k <= a.cgtab_len) ? a.cgtab[a.k0 + k] : cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
+    grams_pi<L>(s, b);                         // its first barrier publishes s_maxit
     regularize<L>(s, b, mu);
-    const int maxit = cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
+    const int maxit = s_maxit;
     const int its = pcg<L>(s, b, mu, maxit, a.tol);
     double pred_drop, step;
     finish_step<L>(s, b, pred_drop, step);
     core_pass<L>(s, b, fsq, ginf);
     if (threadIdx.x == 0) {
+      step = quick_sqrt(step);
       double m = st.mu;
       const double Fn = 0.5 * fsq;
       const double gain = gain_update(st.F, Fn, pred_drop, m);
-      const double e = st.normS > 0.0 ? sqrt(fsq) / st.normS : 0.0;
+      const double e = st.normS > 0.0 ? quick_div(quick_sqrt(fsq), st.normS) : 0.0;
       st.mu = m; st.F = Fn; st.rel_err = e; st.grad_inf = ginf;
       st.cg_total += its; st.iters = k; st.kglob = a.k0 + k;
       a.hist[k] = e;
       write_trace(a.trace, a.trace_cap, a.trace_slot0 + k - 1, a.k0 + k, e, m, gain, its, step,
                   ginf, 0);
       if (!isfinite(fsq) || !isfinite(step)) { st.status = CPD_ERR_NUMERIC; st.stop = CPD_STOP_NONE; }
-      else st.stop = stop_test(k, a.maxiter, a.tol, e, step, ginf, st.normS, a.hist);
+      else st.stop = stop_test(k, a.maxiter, a.tol, e, step, ginf, s_div, a.hist);
     }
     __syncthreads();
     if (st.stop != CPD_STOP_NONE || st.status != CPD_OK) break;
@@ -182,7 +194,9 @@ __global__ void __launch_bounds__(1024) k_dgn_core(DgnArgs a) {
 template <int L>
 __global__ void __launch_bounds__(1024) k_core_eval(CoreEvalArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shape s; make_shape(s, L, a.dims, a.R);
+  __shared__ Shape s;
+  if (threadIdx.x == 0) make_shape(s, L, a.dims, a.R);
+  __syncthreads();
   Bufs b; float* Sbuf;
   carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf);
   double nrm, meanabs;
@@ -201,7 +215,9 @@ __global__ void __launch_bounds__(1024) k_core_eval(CoreEvalArgs a) {
 template <int L>
 __global__ void __launch_bounds__(1024) k_jtj_apply(JtjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shape s; make_shape(s, L, a.dims, a.R);
+  __shared__ Shape s;
+  if (threadIdx.x == 0) make_shape(s, L, a.dims, a.R);
+  __syncthreads();
   Bufs b; float* Sbuf;
   carve(s, b, smem_raw, nullptr, 0, &Sbuf);   // no tensor-sized buffers used
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) { b.W[j] = a.W[j]; b.Tmp[j] = a.V[j]; }

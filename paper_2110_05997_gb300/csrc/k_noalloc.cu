@@ -23,7 +23,8 @@
 namespace cpdk {
 
 // Capacity: result record + error history of up to kNoallocMaxIter + 1
-// iterations + the balanced factors (R * sum(I_l) <= kNoallocMaxParams floats).
+// iterations + the balanced factors (R * sum(I_l) <= kNoallocMaxParams floats)
+// + the table of CG iteration caps (kNoallocMaxIter + 1 ints).
 constexpr size_t kNoallocBytes = 128 * 1024;
 constexpr int kNoallocMaxIter = 4096;
 constexpr int kNoallocMaxParams = 16384;
@@ -100,6 +101,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   DevResult* res = reinterpret_cast<DevResult*>(b);
   double* hist = reinterpret_cast<double*>(b + 256);
   float* Wc = reinterpret_cast<float*>(b + 256 + (((size_t)kNoallocMaxIter + 1) * sizeof(double) + 255) / 256 * 256);
+  int* cgtab = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(Wc) + (size_t)kNoallocMaxParams * sizeof(float));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   // the result record is read back below: clear it so a failed launch cannot
@@ -116,6 +118,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   a.big_in_smem = 1; a.gscratch = nullptr;
   a.hist = hist; a.trace = nullptr; a.trace_cap = 0; a.trace_slot0 = 0;
   a.W_out = Wc; a.res = res;
+  a.cgtab = cgtab; a.cgtab_len = o.maxiter;
   const int threads = o.block_threads > 0 ? o.block_threads : (n > 2048 ? 1024 : 256);
   if (launch_dgn_core(L, a, threads, smem, st) != cudaSuccess) return CPD_ERR_CUDA;
   long long ld[CPD_MAX_ORDER] = {1, 1, 1, 1};

@@ -44,6 +44,8 @@ struct DgnArgs {
   int trace_cap, trace_slot0;
   float* W_out;               // balanced factors, stacked blocks
   DevResult* res;
+  int* cgtab;                 // cg_maxiter(k) for k = 1..cgtab_len, filled in the prologue
+  int cgtab_len;
 };
 
 struct CoreEvalArgs {
@@ -131,6 +133,7 @@ struct RefinePassArgs {
   const int* done;            // skip when *done != 0 (refinement stopped)
 };
 cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st);
+bool refine_pass_supported(int I1, int R);
 
 struct RefineStepArgs {
   int L, R;
@@ -149,6 +152,8 @@ struct RefineStepArgs {
   double* trace;
   int trace_cap, trace_slot0;
   int* done;
+  const int* cgtab;           // cg_maxiter(k) table written by the core solver
+  int cgtab_len;
 };
 size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem);
 cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st);

@@ -89,24 +89,25 @@ __device__ void grams_pi(const Shape& s, const Bufs& b) {
 template <int L>
 __device__ void regularize(const Shape& s, const Bufs& b, double mu) {
   const int R = s.R, RR = R * R;
-  double mx = 0.0;
+  float mx = 0.f;
   for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
     const int l = q / R, r = q - l * R;
-    double p = 1.0;
+    float p = 1.f;
 #pragma unroll
     for (int j = 0; j < L; ++j)
-      if (j != l) p *= sqrt(fmax((double)b.gram[j * RR + r * R + r], 0.0));
-    b.gam[q] = (float)p;
-    mx = fmax(mx, p);
+      if (j != l) p *= sqrtf(fmaxf(b.gram[j * RR + r * R + r], 0.f));
+    b.gam[q] = p;
+    mx = fmaxf(mx, p);
   }
-  const double gmax = block_max(mx, b.red);
+  const float gmax = block_max(mx, b.red);
+  const float muf = (float)mu;
   for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
     const int l = q / R, r = q - l * R;
-    const double g = (double)b.gam[q] * gmax;
-    const double a = (double)b.Pi2[(l * L + l) * RR + r * R + r];
-    b.gam[q] = (float)g;
-    const double m = a + mu * g;
-    b.msq[q] = (float)(m > 0.0 ? 1.0 / sqrt(m) : 1.0);
+    const float g = b.gam[q] * gmax;
+    const float a = b.Pi2[(l * L + l) * RR + r * R + r];
+    b.gam[q] = g;
+    const float m = fmaf(muf, g, a);
+    b.msq[q] = m > 0.f ? rsqrtf(m) : 1.f;
   }
   __syncthreads();
 }
@@ -161,39 +162,44 @@ __device__ __forceinline__ float hv_entry(const Shape& s, const Bufs& b, const f
 template <int L>
 __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
   const int n = s.n, R = s.R;
-  double v[1] = {0.0};
+  float v[1] = {0.f};
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     int l, i, r; decode_j<L>(s, j, l, i, r);
     const float m = b.msq[l * R + r];
     const float rv = m * b.G[j];
     b.Rr[j] = rv; b.P[j] = rv; b.X[j] = 0.f; b.Tmp[j] = m * rv;
-    v[0] += (double)rv * (double)rv;
+    v[0] = fmaf(rv, rv, v[0]);
   }
-  block_sum<1>(v, b.red);
-  double rr = v[0];
+  double rr0[1];
+  block_sum<1>(v, rr0, b.red);
+  double rr = rr0[0];
   int its = 0;
   for (int it = 0; it < maxit; ++it) {
     hv_xy<L>(s, b, b.Tmp);
-    double pz[1] = {0.0};
+    float pzf[1] = {0.f};
+    const float muf = (float)mu;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       int l, i, r; decode_j<L>(s, j, l, i, r);
       const int q = l * R + r;
-      const float z = b.msq[q] * (hv_entry<L>(s, b, b.Tmp, l, i, r) + (float)mu * b.gam[q] * b.Tmp[j]);
+      const float z = b.msq[q] * (hv_entry<L>(s, b, b.Tmp, l, i, r) + muf * b.gam[q] * b.Tmp[j]);
       b.Z[j] = z;
-      pz[0] += (double)b.P[j] * (double)z;
+      pzf[0] = fmaf(b.P[j], z, pzf[0]);
     }
-    block_sum<1>(pz, b.red);
+    double pz[1];
+    block_sum<1>(pzf, pz, b.red);
     if (!(pz[0] > 0.0)) break;
-    const double alpha = rr / pz[0];
-    double rn[1] = {0.0};
+    const double alpha = warp_div(rr, pz[0]);
+    float rnf[1] = {0.f};
+    const float af = (float)alpha;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      b.X[j] = fmaf((float)alpha, b.P[j], b.X[j]);
-      const float rv = fmaf(-(float)alpha, b.Z[j], b.Rr[j]);
+      b.X[j] = fmaf(af, b.P[j], b.X[j]);
+      const float rv = fmaf(-af, b.Z[j], b.Rr[j]);
       b.Rr[j] = rv;
-      rn[0] += (double)rv * (double)rv;
+      rnf[0] = fmaf(rv, rv, rnf[0]);
     }
-    block_sum<1>(rn, b.red);
-    const double beta = rr > 0.0 ? rn[0] / rr : 0.0;
+    double rn[1];
+    block_sum<1>(rnf, rn, b.red);
+    const double beta = rr > 0.0 ? warp_div(rn[0], rr) : 0.0;
     rr = rn[0];
     its = it + 1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -223,14 +229,14 @@ __device__ void balance(const Shape& s, const Bufs& b) {
   __syncthreads();
   for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
     const int l = q / R, r = q - l * R;
-    double lg = 0.0; bool ok = true;
+    float lg = 0.f; bool ok = true;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-      const double nj = (double)b.sc[j * R + r];
-      ok = ok && (nj > 0.0);
-      lg += ok ? log(nj) : 0.0;
+      const float nj = b.sc[j * R + r];
+      ok = ok && (nj > 0.f);
+      lg += ok ? logf(nj) : 0.f;
     }
-    b.gam[q] = ok ? (float)(exp(lg / L) / (double)b.sc[q]) : 1.f;   // gam reused as scratch
+    b.gam[q] = ok ? expf(lg / L) / b.sc[q] : 1.f;   // gam reused as scratch
   }
   __syncthreads();
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
@@ -241,8 +247,8 @@ __device__ void balance(const Shape& s, const Bufs& b) {
 }
 
 // After the PCG: x = M^{-1/2} x_hat (into b.X), the predicted decrease
-// F - ½||f + Jx||^2 = <g, x> - ½<x, J^T J x> (g = A^T b), the step norm, then
-// w += x and balancing.
+// F - ½||f + Jx||^2 = <g, x> - ½<x, J^T J x> (g = A^T b), the squared step
+// norm ||x||^2, then w += x and balancing.
 template <int L>
 __device__ void finish_step(const Shape& s, const Bufs& b, double& pred_drop, double& step) {
   const int R = s.R;
@@ -252,17 +258,18 @@ __device__ void finish_step(const Shape& s, const Bufs& b, double& pred_drop, do
   }
   __syncthreads();
   hv_xy<L>(s, b, b.X);
-  double v[3] = {0.0, 0.0, 0.0};
+  float vf[3] = {0.f, 0.f, 0.f};
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
     int l, i, r; decode_j<L>(s, j, l, i, r);
-    const double x = (double)b.X[j];
-    v[0] += (double)b.G[j] * x;
-    v[1] += x * (double)hv_entry<L>(s, b, b.X, l, i, r);
-    v[2] += x * x;
+    const float x = b.X[j];
+    vf[0] = fmaf(b.G[j], x, vf[0]);
+    vf[1] = fmaf(x, hv_entry<L>(s, b, b.X, l, i, r), vf[1]);
+    vf[2] = fmaf(x, x, vf[2]);
   }
-  block_sum<3>(v, b.red);
+  double v[3];
+  block_sum<3>(vf, v, b.red);
   pred_drop = v[0] - 0.5 * v[1];
-  step = sqrt(v[2]);
+  step = v[2];                      // squared here; the caller's bookkeeping thread takes the root
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] += b.X[j];
   __syncthreads();
   balance<L>(s, b);
@@ -292,16 +299,17 @@ __device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& gi
     }
   }
   __syncthreads();
-  double acc[1] = {0.0};
+  float accf[1] = {0.f};
   for (int e = threadIdx.x; e < N; e += blockDim.x) {
     const int iL = e / NL, q = e - iL * NL;
     float t = 0.f;
     for (int r = 0; r < R; ++r) t = fmaf(b.Kb[r * NL + q], WL[r * dl + iL], t);
     const float f = b.S[e] - t;
     b.F[e] = f;
-    acc[0] += (double)f * (double)f;
+    accf[0] = fmaf(f, f, accf[0]);
   }
-  block_sum<1>(acc, b.red);
+  double acc[1];
+  block_sum<1>(accf, acc, b.red);
   fsq = acc[0];
   // A[r][e'] = sum_{iL} f[e', iL] W_L[iL, r];  B[r][e''] = sum_{i0} f[i0, e''] W_0[i0, r]
   for (int q = threadIdx.x; q < R * NL; q += blockDim.x) {
@@ -320,7 +328,7 @@ __device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& gi
     b.Bb[q] = a;
   }
   __syncthreads();
-  double gm = 0.0;
+  float gm = 0.f;
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
     int l, i, r; decode_j<L>(s, j, l, i, r);
     // source buffer, its strides per mode, and the free modes to sum over
@@ -358,16 +366,16 @@ __device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& gi
       }
     }
     b.G[j] = g;
-    gm = fmax(gm, (double)fabsf(g));
+    gm = fmaxf(gm, fabsf(g));
   }
-  ginf = block_max(gm, b.red);
+  ginf = (double)block_max(gm, b.red);
 }
 
 // Stop tests of Sec. 4.1.3 in the printed order (reading: windows as printed,
 // checked when k is a multiple of c = 1 + ceil(maxiter/10) and k > 2c).
 // hist[j] = relative error after iteration j (hist[0] the starting point).
 __device__ inline int stop_test(int k, int maxiter, double tol, double e, double step,
-                                double ginf, double normS, const double* hist) {
+                                double ginf, double div_thresh, const double* hist) {
   const int c = 1 + (maxiter + 9) / 10;
   if (e < tol) return CPD_STOP_REL_ERR;
   if (step < tol) return CPD_STOP_STEP;
@@ -381,15 +389,27 @@ __device__ inline int stop_test(int k, int maxiter, double tol, double e, double
     if (a1 - a2 < tol) return CPD_STOP_AVG_ERR;
     if (imp < 1e-3 * a2) return CPD_STOP_AVG_IMPROVEMENT;
   }
-  if (e > fmax(1.0, normS * normS) / (1e-16 + tol)) return CPD_STOP_DIVERGENCE;
+  if (e > div_thresh) return CPD_STOP_DIVERGENCE;     // max(1, ||S||^2) / (1e-16 + tol)
   if (k == maxiter) return CPD_STOP_MAXITER;
   return CPD_STOP_NONE;
+}
+
+// Divergence threshold of stop test 7: max(1, ||S||^2) / (1e-16 + tol).
+__device__ inline double divergence_threshold(double normS, double tol) {
+  return fmax(1.0, normS * normS) / (1e-16 + tol);
+}
+
+// cg_maxiter(k) for k = 1..len into tab[k] by all threads of the CTA (the FP64
+// powers are computed once per solve, in parallel).  Ends with a barrier.
+__device__ inline void fill_cg_table(int* tab, int len, uint64_t seed, double ca, double cb) {
+  for (int k = threadIdx.x + 1; k <= len; k += blockDim.x) tab[k] = cg_maxiter(k, seed, ca, cb);
+  __syncthreads();
 }
 
 // Gain ratio (Sec. 3.3.1 / 4.1.3) and the damping update x3 below 0.25,
 // /3 above 0.75 (the rule Sec. 4.1.3 settles on).
 __device__ inline double gain_update(double F_old, double F_new, double pred_drop, double& mu) {
-  const double g = pred_drop > 0.0 ? (F_old - F_new) / pred_drop : 0.0;
+  const double g = pred_drop > 0.0 ? quick_div(F_old - F_new, pred_drop) : 0.0;
   if (g < 0.25) mu *= 3.0;
   else if (g > 0.75) mu /= 3.0;
   return g;
