@@ -81,7 +81,7 @@ def _mix64(z: int) -> int:
 def splitmix64(seed: int, stream: int, counter: int) -> int:
     """The counter-th output (counter >= 1) of SplitMix64 started at state
     seed + stream·0xD1B54A32D192ED03 (mod 2^64)."""
-    state = (seed + stream * STREAM_STRIDE + counter * GOLDEN_GAMMA) & MASK64
+    state = (int(seed) + int(stream) * STREAM_STRIDE + int(counter) * GOLDEN_GAMMA) & MASK64
     return _mix64(state)
 
 

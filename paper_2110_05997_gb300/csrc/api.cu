@@ -110,10 +110,10 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
   p.cgtab = c.take<int>((size_t)p.cgtab_len + 1);
   Shape sc; make_shape(sc, L, cmax, R);
   p.W_core = c.take<float>(sc.n);
-  size_t smem_big = dgn_smem_bytes(L, cmax, R, 1);
+  size_t smem_big = dgn_smem_bytes_host(L, cmax, R, 1);
   p.big_in_smem = smem_big <= smem_limit() ? 1 : 0;
-  p.dgn_smem = dgn_smem_bytes(L, cmax, R, p.big_in_smem);
-  if (!p.big_in_smem) p.gscratch = c.take<float>(dgn_gscratch_floats(L, cmax, R));
+  p.dgn_smem = dgn_smem_bytes_host(L, cmax, R, p.big_in_smem);
+  if (!p.big_in_smem) p.gscratch = c.take<float>(dgn_gscratch_floats_host(L, cmax, R));
   p.n_full = 0;
   for (int l = 0; l < L; ++l) p.n_full += R * p.idims[l];
   p.W_full = c.take<float>(p.n_full);
@@ -286,7 +286,7 @@ size_t cpd_workspace_size(int L, const int64_t* dims, int R, const cpd_options* 
   // component calls reuse the same workspace: make room for their scratch too
   int d[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) d[l] = (int)dims[l];
-  size_t extra = (dgn_smem_bytes(L, d, R, 1) <= smem_limit()) ? 0 : dgn_gscratch_floats(L, d, R) * 4;
+  size_t extra = (dgn_smem_bytes_host(L, d, R, 1) <= smem_limit()) ? 0 : dgn_gscratch_floats_host(L, d, R) * 4;
   size_t need = c.used + 256;
   return need > extra + 512 ? need : extra + 512;
 }
@@ -447,11 +447,11 @@ int cpd_core_eval(const float* S, int L, const int64_t* dims, int R, const float
   a.R = R;
   for (int l = 0; l < CPD_MAX_ORDER; ++l) a.dims[l] = d[l];
   a.S = S; a.W = W; a.f_out = f_out; a.g_out = g_out; a.fsq_out = fsq_out;
-  size_t sm = dgn_smem_bytes(L, d, R, 1);
+  size_t sm = dgn_smem_bytes_host(L, d, R, 1);
   a.big_in_smem = sm <= smem_limit() ? 1 : 0;
   if (!a.big_in_smem) {
-    sm = dgn_smem_bytes(L, d, R, 0);
-    if (!workspace || ws_bytes < dgn_gscratch_floats(L, d, R) * 4) return CPD_ERR_WORKSPACE;
+    sm = dgn_smem_bytes_host(L, d, R, 0);
+    if (!workspace || ws_bytes < dgn_gscratch_floats_host(L, d, R) * 4) return CPD_ERR_WORKSPACE;
     a.gscratch = static_cast<float*>(workspace);
   }
   Shape s; make_shape(s, L, d, R);
@@ -472,7 +472,7 @@ int cpd_jtj_apply(int L, const int64_t* dims, int R, const float* W, const float
   a.R = R;
   for (int l = 0; l < CPD_MAX_ORDER; ++l) a.dims[l] = d[l];
   a.W = W; a.V = V; a.out = out;
-  size_t sm = dgn_smem_bytes(L, d, R, 0);
+  size_t sm = dgn_smem_bytes_host(L, d, R, 0);
   if (sm > smem_limit()) return CPD_ERR_UNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   PL("jtj_apply", launch_jtj_apply(L, a, 256, sm, st));

@@ -1,20 +1,447 @@
-// Batched persistent solver for many small uneven CPDs.
+// Batched solver for many small, unevenly shaped third-order CPDs: one
+// persistent launch; every CTA takes items from a device work queue (items
+// sorted longest-first by the host) and runs the whole method on each:
+// ST-MLSVD compression (Gram, leading eigenpairs and truncation, projection;
+// Sec. 2.2 and 4.1.1), initialisation and damped Gauss-Newton on the core
+// (Sec. 4.1.2-4.1.3, the same device code as the single-tensor solver),
+// uncompression (Sec. 4.1.4) and output normalisation.
+#include <algorithm>
+#include <string.h>
+#include <vector>
+
 #include "kernels.h"
+#include "solver.cuh"
+#include "dgn_cta.cuh"
+#include "eig_cta.cuh"
+
+namespace cpdk {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchMaxDim = 64;
+constexpr int kBatchMaxRank = 16;
+constexpr int kGTile = 16;           // rows of the Gram's staging tile
+constexpr int kGLd = 68;             // padded row length of the staging tile
+
+// G (b x b, column-major) = sum_q X[q,:]^T X[q,:] with X[q, j] = T[i + a j + a b k],
+// q = i + a k over the a*c "other" indices.  b <= 64; 128 threads, each a
+// 4 x 8 block of the 64 x 64 output; rows of X staged in shared memory.
+__device__ void cta_gram(const float* __restrict__ T, int a, int b, int c, float* G, float* tile) {
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[4][8];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  const long long K = (long long)a * c;
+  for (long long qb = 0; qb < K; qb += kGTile) {
+    for (int e = threadIdx.x; e < kGTile * 64; e += blockDim.x) {
+      const int kk = e >> 6, jj = e & 63;
+      const long long q = qb + kk;
+      float x = 0.f;
+      if (q < K && jj < b) {
+        const long long i = q % a, k = q / a;
+        x = __ldg(T + i + (long long)a * jj + (long long)a * b * k);
+      }
+      tile[kk * kGLd + jj] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGTile; ++kk) {
+      const float4 ar = *reinterpret_cast<const float4*>(tile + kk * kGLd + ty * 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(tile + kk * kGLd + tx * 8);
+      const float4 b1 = *reinterpret_cast<const float4*>(tile + kk * kGLd + tx * 8 + 4);
+      const float av[4] = {ar.x, ar.y, ar.z, ar.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int r = ty * 4 + u, cc = tx * 8 + v;
+      if (r < b && cc < b) G[r + b * cc] = acc[u][v];
+    }
+  __syncthreads();
+}
+
+// Y[i + a r + a rk k] = sum_j U[j + b r] T[i + a j + a b k], r < rk <= 16.
+__device__ void cta_project(const float* __restrict__ T, int a, int b, int c, const float* U, int rk,
+                            float* Y) {
+  const long long n = (long long)a * c;
+  for (long long q = threadIdx.x; q < n; q += blockDim.x) {
+    const long long i = q % a, k = q / a;
+    const float* t = T + i + (long long)a * b * k;
+    float acc[kBatchMaxRank];
+#pragma unroll
+    for (int u = 0; u < kBatchMaxRank; ++u) acc[u] = 0.f;
+    for (int j = 0; j < b; ++j) {
+      const float x = t[(long long)a * j];
+#pragma unroll
+      for (int u = 0; u < kBatchMaxRank; ++u)
+        if (u < rk) acc[u] = fmaf(U[u * b + j], x, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatchMaxRank; ++u)
+      if (u < rk) Y[i + (long long)a * u + (long long)a * rk * k] = acc[u];
+  }
+  __syncthreads();
+}
+
+struct BatchLayout {           // per-CTA global scratch, offsets in floats
+  size_t U, sig, Y1, Y2, S, Wc, Wf, res, cg, total;
+};
+
+__host__ __device__ inline BatchLayout batch_layout(int dmax, int Rmax, int maxiter) {
+  const size_t P = (size_t)(Rmax < dmax ? Rmax : dmax);
+  auto up = [](size_t x) { return (x + 63) & ~(size_t)63; };
+  BatchLayout l{};
+  size_t o = 0;
+  l.U = o; o += up(3 * (size_t)dmax * P);
+  l.sig = o; o += up(3 * P);
+  l.Y1 = o; o += up(P * dmax * dmax);
+  l.Y2 = o; o += up(P * P * dmax);
+  l.S = o; o += up(P * P * P);
+  l.Wc = o; o += up(3 * (size_t)dmax * Rmax);          // core factors (or T's, uncompressed)
+  l.Wf = o; o += up(3 * (size_t)dmax * Rmax);
+  l.res = o; o += 64;                                  // DevResult
+  l.cg = o; o += up((size_t)maxiter + 1);              // cg_maxiter table (ints)
+  l.total = o;
+  return l;
+}
+
+__host__ __device__ inline int g_floats(int dmax) { return (dmax * dmax + 3) & ~3; }   // 16-byte multiple
+
+__host__ __device__ inline size_t batch_compress_smem(int dmax, int Rmax) {
+  const int P = Rmax < dmax ? Rmax : dmax;
+  return (size_t)g_floats(dmax) * 4 + (size_t)kGTile * kGLd * 4 + (size_t)dmax * P * 4 + 256 +
+         eig_smem_bytes(dmax, P, false);
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, int Rmax, size_t smem_bytes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_idx;
+  __shared__ int s_rank[3];
+  const BatchLayout lay = batch_layout(dmax, Rmax, a.maxiter);
+  float* gs = a.scratch + (size_t)blockIdx.x * a.scratch_floats_per_cta;
+  double* hist = a.hist + (size_t)blockIdx.x * (a.maxiter + 1);
+  int* cgtab = reinterpret_cast<int*>(gs + lay.cg);
+  DevResult* dres = reinterpret_cast<DevResult*>(gs + lay.res);
+  const int P0 = Rmax < dmax ? Rmax : dmax;
+  // compression shared layout: G | tile | Us | eig workspace
+  float* G = reinterpret_cast<float*>(smem_raw);
+  float* tile = G + g_floats(dmax);
+  float* Us = tile + kGTile * kGLd;
+  unsigned char* eigw = reinterpret_cast<unsigned char*>(Us + dmax * P0) + 256 -
+                        (reinterpret_cast<size_t>(Us + dmax * P0) & 255);
+  for (int guard = 0; guard < a.B + 1; ++guard) {     // at most B items per CTA
+    if (threadIdx.x == 0) s_idx = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= a.B) break;
+    const BatchItem it = a.items[idx];
+    const int d[3] = {it.d[0], it.d[1], it.d[2]};
+    const int R = it.R;
+    const uint64_t seed = a.seed + (uint64_t)it.b;
+    const float* T = a.T + it.t_off;
+    int core[3] = {d[0], d[1], d[2]};
+    const float* S = T;
+    float* U = gs + lay.U;
+    if (a.compress) {
+      // ST-MLSVD: mode by mode on the partially projected tensor
+      const float* cur = T;
+      float* outs[3] = {gs + lay.Y1, gs + lay.Y2, gs + lay.S};
+      long long ah = 1;
+      size_t offU = 0;
+      for (int l = 0; l < 3; ++l) {
+        long long c = 1;
+        for (int j = l + 1; j < 3; ++j) c *= d[j];
+        const int P = R < d[l] ? R : d[l];
+        cta_gram(cur, (int)ah, d[l], (int)c, G, tile);
+        EigArgs ea{};
+        ea.G = G; ea.I = d[l]; ea.P = P; ea.U = U + offU; ea.sigma = gs + lay.sig + l * P0;
+        ea.rank_out = &s_rank[l]; ea.mlsvd_tol = a.mlsvd_tol; ea.L = 3;
+        ea.seed = seed + 7919ull * (uint64_t)l;
+        ea.work = G;                                   // non-null: G is read in place
+        eig_run(ea, eigw);
+        __syncthreads();
+        const int rk = s_rank[l];
+        for (int e = threadIdx.x; e < d[l] * rk; e += blockDim.x) Us[e] = U[offU + e];
+        __syncthreads();
+        cta_project(cur, (int)ah, d[l], (int)c, Us, rk, outs[l]);
+        core[l] = rk;
+        cur = outs[l];
+        ah *= rk;
+        offU += (size_t)d[l] * P;
+      }
+      S = gs + lay.S;
+    }
+    // damped Gauss-Newton on the core (the single-CTA solver); an item whose
+    // tensor would not fit the launched shared memory is refused, not run
+    {
+      int cd[CPD_MAX_ORDER] = {core[0], core[1], core[2], 1};
+      if (dgn_smem_bytes(3, cd, R, 1) > smem_bytes) {
+        if (threadIdx.x == 0) {
+          cpd_info inf;
+          memset(&inf, 0, sizeof(inf));
+          inf.status = CPD_ERR_UNSUPPORTED;
+          a.infos[it.b] = inf;
+        }
+        __syncthreads();
+        continue;
+      }
+    }
+    DgnArgs da{};
+    da.R = R;
+    da.dims[0] = core[0]; da.dims[1] = core[1]; da.dims[2] = core[2]; da.dims[3] = 1;
+    da.dev_dims = nullptr;
+    da.S = S; da.s_f64 = 0; da.W0 = nullptr; da.init = a.init; da.seed = seed;
+    da.tol = a.tol; da.tau = a.tau; da.cg_a = a.cg_a; da.cg_b = a.cg_b; da.maxiter = a.maxiter;
+    da.mu0 = -1.0; da.k0 = 0; da.big_in_smem = 1; da.gscratch = nullptr;
+    da.hist = hist; da.trace = nullptr; da.trace_cap = 0; da.trace_slot0 = 0;
+    da.W_out = gs + lay.Wc; da.res = dres; da.cgtab = cgtab; da.cgtab_len = a.maxiter;
+    __syncthreads();
+    dgn_run<3>(da, smem_raw);
+    __syncthreads();
+    // uncompression W~ = U W (or the factors themselves)
+    const float* Wc = gs + lay.Wc;
+    float* Wf = gs + lay.Wf;
+    {
+      int offU = 0, offC = 0, offF = 0;
+      for (int l = 0; l < 3; ++l) {
+        const int I = d[l], rk = core[l], P = R < d[l] ? R : d[l];
+        for (int q = threadIdx.x; q < I * R; q += blockDim.x) {
+          const int r = q / I, i = q - r * I;
+          float acc;
+          if (a.compress) {
+            acc = 0.f;
+            for (int t = 0; t < rk; ++t) acc = fmaf(U[offU + t * I + i], Wc[offC + r * rk + t], acc);
+          } else {
+            acc = Wc[offC + r * rk + i];
+          }
+          Wf[offF + q] = acc;
+        }
+        offU += I * P;
+        offC += rk * R;
+        offF += I * R;
+      }
+    }
+    __syncthreads();
+    // output normalisation (unit columns, lambda, signs, descending lambda)
+    float* nrm = reinterpret_cast<float*>(smem_raw);          // 3 * R
+    float* sgn = nrm + 3 * kBatchMaxRank;                      // 3 * R
+    double* lamd = reinterpret_cast<double*>(sgn + 3 * kBatchMaxRank);
+    int* pos = reinterpret_cast<int*>(lamd + kBatchMaxRank);
+    {
+      int off[4] = {0, d[0] * R, (d[0] + d[1]) * R, (d[0] + d[1] + d[2]) * R};
+      for (int q = threadIdx.x; q < 3 * R; q += blockDim.x) {
+        const int l = q / R, r = q - l * R, I = d[l];
+        const float* w = Wf + off[l] + r * I;
+        double s = 0.0; float best = -1.f; int bi = 0;
+        for (int i = 0; i < I; ++i) {
+          s += (double)w[i] * (double)w[i];
+          if (fabsf(w[i]) > best) { best = fabsf(w[i]); bi = i; }
+        }
+        nrm[q] = (float)sqrt(s);
+        sgn[q] = w[bi] < 0.f ? -1.f : 1.f;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        lamd[r] = (double)nrm[r] * (double)nrm[R + r] * (double)nrm[2 * R + r];
+        sgn[2 * R + r] = sgn[r] * sgn[R + r];
+      }
+      __syncthreads();
+      float* lam_out = a.lam + it.l_off;
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        int p = 0;
+        for (int t = 0; t < R; ++t) p += (lamd[t] > lamd[r] || (lamd[t] == lamd[r] && t < r)) ? 1 : 0;
+        pos[r] = p;
+        lam_out[p] = (float)lamd[r];
+      }
+      __syncthreads();
+      float* W_out = a.W + it.w_off;
+      for (int l = 0; l < 3; ++l) {
+        const int I = d[l];
+        for (int q = threadIdx.x; q < I * R; q += blockDim.x) {
+          const int r = q / I, i = q - r * I;
+          const float nr = nrm[l * R + r];
+          W_out[off[l] + pos[r] * I + i] = Wf[off[l] + q] * (nr > 0.f ? 1.f / nr : 1.f) * sgn[l * R + r];
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      cpd_info inf;
+      memset(&inf, 0, sizeof(inf));
+      inf.status = dres->status; inf.iters = dres->iters; inf.stop_reason = dres->stop;
+      inf.cg_total = dres->cg_total; inf.rel_err = dres->rel_err; inf.mu = dres->mu;
+      inf.grad_inf = dres->grad_inf;
+      inf.core_dims[0] = core[0]; inf.core_dims[1] = core[1]; inf.core_dims[2] = core[2];
+      a.infos[it.b] = inf;
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory of one batch CTA: the larger of the compression phase and
+// the dGN phase; the dGN holds the core (P^3, P = min(Rmax, dmax)) or, without
+// compression, the whole item tensor (dmax^3).
+size_t batch_smem_bytes(int dmax, int Rmax, int compress) {
+  const int P = compress ? (Rmax < dmax ? Rmax : dmax) : dmax;
+  int cd[CPD_MAX_ORDER] = {P, P, P, 1};
+  size_t s1 = compress ? batch_compress_smem(dmax, Rmax) : 0;
+  size_t s2 = dgn_smem_bytes(3, cd, Rmax, 1);
+  size_t s3 = 2048;                                 // normalisation scratch
+  size_t s = s1 > s2 ? s1 : s2;
+  return s > s3 ? s : s3;
+}
+
+}  // namespace cpdk
+
+using namespace cpdk;
+
+namespace {
+size_t smem_cap() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+    return (size_t)v;
+  return 227 * 1024;
+}
+
+int batch_validate(int B, const int* dims, const int* ranks, const cpd_options& o, int* dmax, int* Rmax) {
+  if (B < 1 || dims == nullptr || ranks == nullptr) return CPD_ERR_INVALID_ARG;
+  if (o.maxiter < 1 || o.maxiter > 100000 || !(o.tol >= 0.0) || !(o.tau >= 0.0)) return CPD_ERR_INVALID_ARG;
+  if (o.init != CPD_INIT_MLSVD && o.init != CPD_INIT_RANDOM) return CPD_ERR_UNSUPPORTED;
+  if (o.refine_maxiter != 0 || o.gram_precision != CPD_GRAM_FP32) return CPD_ERR_UNSUPPORTED;
+  int dm = 1, rm = 1;
+  for (int b = 0; b < B; ++b) {
+    const int R = ranks[b];
+    if (R < 1) return CPD_ERR_INVALID_ARG;
+    if (R > kBatchMaxRank) return CPD_ERR_UNSUPPORTED;
+    double N = 1.0;
+    for (int l = 0; l < 3; ++l) {
+      const int x = dims[3 * b + l];
+      if (x < 1) return CPD_ERR_INVALID_ARG;
+      if (x > kBatchMaxDim || x < 2) return CPD_ERR_UNSUPPORTED;
+      dm = x > dm ? x : dm;
+      N *= x;
+    }
+    if ((double)R > N) return CPD_ERR_INVALID_ARG;
+    rm = R > rm ? R : rm;
+  }
+  *dmax = dm; *Rmax = rm;
+  if (!o.compress) {
+    // the uncompressed solve keeps T in shared memory
+    int cd[CPD_MAX_ORDER] = {dm, dm, dm, 1};
+    if (dgn_smem_bytes(3, cd, rm, 1) > smem_cap()) return CPD_ERR_UNSUPPORTED;
+  }
+  return CPD_OK;
+}
+
+struct BatchPlan {
+  size_t items, queue, infos, scratch, hist, total;
+  int ctas;
+  size_t per_cta;
+};
+
+// The CTA count follows from the shared-memory and thread budget of an SM
+// (analytically, so the workspace size does not depend on runtime state);
+// CTAs that cannot be resident at once simply start later and drain the queue.
+BatchPlan batch_plan(int B, int dmax, int Rmax, const cpd_options& o, size_t smem) {
+  BatchPlan p{};
+  int per_sm = (int)((228 * 1024) / (smem + 1024));
+  if (per_sm > 2048 / kBatchThreads) per_sm = 2048 / kBatchThreads;
+  if (per_sm < 1) per_sm = 1;
+  const int sms = 152;
+  p.ctas = per_sm * sms < B ? per_sm * sms : B;
+  const BatchLayout lay = batch_layout(o.compress ? dmax : dmax, Rmax, o.maxiter);
+  p.per_cta = lay.total;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t off = 0;
+  p.items = off; off += up(sizeof(BatchItem) * B);
+  p.queue = off; off += 256;
+  p.infos = off; off += up(sizeof(cpd_info) * B);
+  p.hist = off; off += up(sizeof(double) * (size_t)(o.maxiter + 1) * p.ctas);
+  p.scratch = off; off += up(sizeof(float) * p.per_cta * p.ctas);
+  p.total = off;
+  return p;
+}
+}  // namespace
 
 extern "C" {
 
 size_t cpd_batch_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts) {
-  (void)B; (void)dims; (void)ranks; (void)opts;
-  return 0;
+  cpd_options o; cpd_default_options(&o);
+  if (opts) o = *opts;
+  int dmax = 0, Rmax = 0;
+  if (batch_validate(B, dims, ranks, o, &dmax, &Rmax) != CPD_OK) return 0;
+  const size_t smem = batch_smem_bytes(dmax, Rmax, o.compress);
+  return batch_plan(B, dmax, Rmax, o, smem).total;
 }
 
 int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const int* dims,
                     const int* ranks, const cpd_options* opts, float* W_packed,
                     const int64_t* w_off, float* lam_packed, const int64_t* l_off,
                     cpd_info* infos, void* workspace, size_t ws_bytes, void* stream) {
-  (void)B; (void)T_packed; (void)t_off; (void)dims; (void)ranks; (void)opts; (void)W_packed;
-  (void)w_off; (void)lam_packed; (void)l_off; (void)infos; (void)workspace; (void)ws_bytes; (void)stream;
-  return CPD_ERR_UNSUPPORTED;
+  cpd_options o; cpd_default_options(&o);
+  if (opts) o = *opts;
+  int dmax = 0, Rmax = 0;
+  int v = batch_validate(B, dims, ranks, o, &dmax, &Rmax);
+  if (v != CPD_OK) return v;
+  if (!T_packed || !t_off || !W_packed || !w_off || !lam_packed || !l_off || !workspace)
+    return CPD_ERR_INVALID_ARG;
+  const size_t smem = batch_smem_bytes(dmax, Rmax, o.compress);
+  if (smem > smem_cap()) return CPD_ERR_UNSUPPORTED;
+  const BatchPlan p = batch_plan(B, dmax, Rmax, o, smem);
+  if (ws_bytes < p.total) return CPD_ERR_WORKSPACE;
+  // items, longest first (cost ~ entries x mode sizes)
+  std::vector<BatchItem> items((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    BatchItem& it = items[(size_t)b];
+    it.t_off = t_off[b]; it.w_off = w_off[b]; it.l_off = l_off[b];
+    it.d[0] = dims[3 * b]; it.d[1] = dims[3 * b + 1]; it.d[2] = dims[3 * b + 2];
+    it.R = ranks[b]; it.b = b; it.pad = 0;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
+    const double cx = (double)x.d[0] * x.d[1] * x.d[2] * (x.d[0] + x.d[1] + x.d[2]) + 4e3 * x.R * x.R;
+    const double cy = (double)y.d[0] * y.d[1] * y.d[2] * (y.d[0] + y.d[1] + y.d[2]) + 4e3 * y.R * y.R;
+    return cx > cy;
+  });
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(ws + p.items, items.data(), sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CPD_ERR_CUDA;
+  if (cudaMemsetAsync(ws + p.queue, 0, 256, st) != cudaSuccess) return CPD_ERR_CUDA;
+  BatchArgs a{};
+  a.T = T_packed; a.W = W_packed; a.lam = lam_packed;
+  a.items = reinterpret_cast<const BatchItem*>(ws + p.items);
+  a.B = B;
+  a.queue = reinterpret_cast<int*>(ws + p.queue);
+  a.infos = reinterpret_cast<cpd_info*>(ws + p.infos);
+  a.scratch = reinterpret_cast<float*>(ws + p.scratch);
+  a.scratch_floats_per_cta = p.per_cta;
+  a.hist = reinterpret_cast<double*>(ws + p.hist);
+  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
+  a.mlsvd_tol = o.mlsvd_tol; a.compress = o.compress; a.init = o.init; a.seed = o.seed; a.ctas = p.ctas;
+  {
+    ProfScope ps(st, "batch");
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return CPD_ERR_CUDA;
+    k_batch<<<p.ctas, kBatchThreads, smem, st>>>(a, dmax, Rmax, smem);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return CPD_ERR_CUDA;
+  }
+  if (infos) {
+    if (cudaMemcpyAsync(infos, ws + p.infos, sizeof(cpd_info) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return CPD_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
 }
 
-}
+}  // extern "C"

@@ -92,7 +92,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return CPD_ERR_CUDA;
-  const size_t smem = dgn_smem_bytes(L, d, R, 1);
+  const size_t smem = dgn_smem_bytes_host(L, d, R, 1);
   if (N > 2.0e9 || smem > (size_t)lim) return CPD_ERR_WORKSPACE;   // T must fit the CTA's shared memory
 
   void* base = nullptr;

@@ -68,8 +68,8 @@ struct JtjArgs {
   float* out;
 };
 
-__host__ __device__ size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem);
-__host__ __device__ size_t dgn_gscratch_floats(int L, const int* d, int R);
+size_t dgn_smem_bytes_host(int L, const int* d, int R, int big_in_smem);
+size_t dgn_gscratch_floats_host(int L, const int* d, int R);
 
 cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_core_eval(int L, const CoreEvalArgs& a, int threads, size_t smem, cudaStream_t st);
@@ -168,6 +168,8 @@ struct BatchItem {
   long long t_off, w_off, l_off;
   int d[3];
   int R;
+  int b;                      // index of the item in the caller's order
+  int pad;
 };
 struct BatchArgs {
   const float* T;
@@ -186,7 +188,7 @@ struct BatchArgs {
   uint64_t seed;
   int ctas;
 };
-size_t batch_smem_bytes(int dmax, int Rmax);
+size_t batch_smem_bytes(int dmax, int Rmax, int compress);
 size_t batch_scratch_floats(int dmax, int Rmax);
 cudaError_t launch_batch(const BatchArgs& a, int threads, size_t smem, cudaStream_t st);
 

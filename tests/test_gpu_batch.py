@@ -1,0 +1,146 @@
+"""GPU parity of the batched solver (one persistent launch, one CTA per CPD)
+against the FP64 oracle run item by item with the same options and seeds.
+
+Parity is asserted where the method itself reaches the noise floor on the
+oracle's side (planted problems with the MLSVD-energy start occasionally
+stall in a local minimum; those items are counted and excluded, and most
+items must converge).  These workloads have noise 1e-6 = tol: the
+improvement stop test (|e_{k-1} - e_k| < tol) then fires at an iteration
+that depends on rounding, so FP32 and FP64 runs end a few iterations apart
+and their fits differ by up to a few tol.  The bar is therefore: a large
+majority of items within 1e-6 absolute of the oracle's fit (with factors
+within 1e-4 after alignment), and every converged item within 5e-6."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cpd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_05997_gb300 import build as b
+    b.build()
+    from paper_2110_05997_gb300 import cpd as m
+    m.lib()
+    return m
+
+
+def pack(items):
+    offs, o = [], 0
+    for it in items:
+        offs.append(o)
+        o += it["T"].size
+    flat = np.concatenate([synth.flat(it["T"]).astype(np.float32) for it in items])
+    return torch.from_numpy(flat).cuda(), offs
+
+
+def unpack(W, lam, w_off, l_off, dims, R):
+    Ws, o = [], w_off
+    w = W[o:o + R * sum(dims)].double().cpu().numpy()
+    k = 0
+    for d in dims:
+        Ws.append(w[k:k + d * R].reshape((d, R), order="F"))
+        k += d * R
+    return Ws, lam[l_off:l_off + R].double().cpu().numpy()
+
+
+def run_batch(cpd, items, **kw):
+    Tp, offs = pack(items)
+    dims = [list(it["T"].shape) for it in items]
+    ranks = [it["R"] for it in items]
+    opts = cpd.cpd_default_options(**kw)
+    W, lam, w_off, l_off, infos = cpd.cpd_batch_solve(Tp, offs, dims, ranks, opts)
+    torch.cuda.synchronize()
+    return [unpack(W, lam, w_off[b], l_off[b], dims[b], ranks[b]) for b in range(len(items))], infos
+
+
+def check_item(it, Wg, lg, seed, rel_eta):
+    """Returns None when the oracle stalls (not converged), else True when the
+    GPU result meets the 1e-6 fit bar (factors then checked), False when it
+    does not (but is within 5e-6)."""
+    T = it["T"].astype(np.float64)
+    Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=int(seed)))
+    fo, fg = O.fit(T, Wo, lo), O.fit(T, Wg, lg)
+    if fo >= 10 * rel_eta:
+        return None
+    assert abs(fg - fo) <= 5e-6, (fg, fo, it["T"].shape, it["R"])
+    if abs(fg - fo) > 1e-6:
+        return False
+    c = O.compare_cpd(Wg, lg, Wo, lo)
+    assert max(c["mode_err"]) <= 1e-4 and c["lam_err"] <= 1e-4, c
+    return True
+
+
+def summarize(results, min_converged, min_within):
+    conv = [r for r in results if r is not None]
+    assert len(conv) >= min_converged * len(results), (len(conv), len(results))
+    assert sum(conv) >= min_within * len(conv), (sum(conv), len(conv))
+
+
+def test_batch_small_uneven_matches_oracle(cpd):
+    items = synth.c4_batch(seed=7, B=48, lo=6, hi=20, rlo=1, rhi=6, eta=1e-6)
+    res, infos = run_batch(cpd, items, seed=11)
+    out = []
+    for b, (it, (Wg, lg)) in enumerate(zip(items, res)):
+        assert infos[b]["status"] == 0
+        out.append(check_item(it, Wg, lg, 11 + b, 1e-6))
+    summarize(out, 0.8, 0.85)
+
+
+def test_batch_equals_single_solves(cpd):
+    items = synth.c4_batch(seed=8, B=6, lo=8, hi=30, rlo=2, rhi=8, eta=1e-6)
+    res, infos = run_batch(cpd, items, seed=3)
+    for b, it in enumerate(items):
+        T = it["T"]
+        opts = cpd.cpd_default_options(seed=3 + b)
+        W, lam, info, _ = cpd.cpd_dgn_solve(torch.from_numpy(synth.flat(T)).cuda(), T.shape, it["R"], opts)
+        torch.cuda.synchronize()
+        Ws = [w.double().cpu().numpy() for w in W]
+        ls = lam.double().cpu().numpy()
+        T64 = T.astype(np.float64)
+        assert abs(O.fit(T64, Ws, ls) - O.fit(T64, *res[b])) <= 1e-6
+        assert infos[b]["core_dims"][:3] == info["core_dims"][:3]
+
+
+def test_batch_edge_shapes(cpd):
+    rng = np.random.default_rng(0)
+    shapes = [((2, 2, 2), 1), ((2, 9, 3), 2), ((64, 3, 5), 3), ((5, 64, 64), 4), ((7, 7, 7), 7)]
+    items = []
+    for i, (dims, R) in enumerate(shapes):
+        T, Wt = synth.planted(500 + i, dims, R, 0.0, 1e-6, np.float32)
+        items.append(dict(T=T, R=R, W_true=Wt))
+    res, infos = run_batch(cpd, items, seed=1)
+    out = []
+    for b, it in enumerate(items):
+        assert infos[b]["status"] == 0
+        out.append(check_item(it, *res[b], 1 + b, 1e-6))
+    summarize(out, 0.6, 0.6)
+
+
+def test_batch_uncompressed(cpd):
+    items = synth.c4_batch(seed=9, B=8, lo=4, hi=9, rlo=1, rhi=3, eta=1e-6)
+    res, infos = run_batch(cpd, items, seed=2, compress=0)
+    for b, it in enumerate(items):
+        T = it["T"].astype(np.float64)
+        Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=2 + b, compress=False))
+        fo, fg = O.fit(T, Wo, lo), O.fit(T, *res[b])
+        if fo < 1e-5:
+            assert abs(fg - fo) <= 1e-6
+
+
+def test_batch_full_4096_sampled_parity(cpd):
+    """The uneven-batch workload: 4096 FP32 tensors, modes U{8..48}, ranks U{2..8},
+    noise 1e-6; every item solved, a seeded sample checked against the oracle."""
+    items = synth.c4_batch()
+    res, infos = run_batch(cpd, items, seed=0)
+    assert all(inf["status"] == 0 for inf in infos)
+    assert all(1 <= inf["stop"] <= 8 for inf in infos)
+    pick = np.random.default_rng(123).choice(len(items), size=32, replace=False)
+    out = [check_item(items[int(b)], *res[int(b)], int(b), 1e-6) for b in pick]
+    summarize(out, 0.75, 0.85)
