@@ -202,6 +202,21 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _timed_steps(torch, step, flush, stream, K):
+    """K steps, each bracketed by CUDA events on the launching stream, with an
+    L2 flush (256 MB write) between steps outside the events."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    out = []
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        out.append(step())
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2110_05997_gb300 import build as bld
@@ -210,71 +225,63 @@ def run_ours(args, rank, world, local_rank):
     bld.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)          # a capturable stream: solves replay CUDA graphs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    if args.workload == "batch":
+        return run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush)
     T, R = workload()
     dims = T.shape
     T_flat = synth.flat(T)
     Td = torch.from_numpy(T_flat).to(dev)
     opts = cpd.cpd_default_options(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram)
     ws = torch.empty(cpd.cpd_workspace_size(dims, R, opts), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
-    stream = torch.cuda.current_stream()
 
     def step():
         return cpd.cpd_dgn_solve(Td, dims, R, opts, stream=stream, workspace=ws)
 
-    for _ in range(args.warmup):
-        W, lam, info, _ = step()
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    l0 = cpd.cpd_launch_count()
-    cpd.cpd_profile_enable(True)
-    infos = []
-    with ClockSampler(local_rank) as clk:
-        for i in range(args.steps):
-            flush.zero_()                       # evict T (32 MB) from L2 between steps
-            starts[i].record(stream)
-            W, lam, info, _ = step()
-            ends[i].record(stream)
-            infos.append(info)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
         torch.cuda.synchronize()
-    prof = cpd.cpd_profile_read()
-    cpd.cpd_profile_enable(False)
-    launches = cpd.cpd_launch_count() - l0
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms * 1e-3)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = cpd.cpd_launch_count()
+        with ClockSampler(local_rank) as clk:
+            ms, outs = _timed_steps(torch, step, flush, stream, args.steps)
+        launches = cpd.cpd_launch_count() - l0
+        W, lam, info, _ = outs[-1]
+        infos = [o[2] for o in outs]
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * args.steps / (ms * 1e-3)
 
-    # end to end through the C ABI with host buffers: H2D of T, solve, D2H of W and lambda
-    Th = torch.from_numpy(T_flat).pin_memory()
-    Tdev2 = torch.empty_like(Td)
-    n_out = R * sum(dims)
-    Wh = torch.empty(n_out, dtype=torch.float32).pin_memory()
-    lh = torch.empty(R, dtype=torch.float32).pin_memory()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        e0[i].record(stream)
-        Tdev2.copy_(Th, non_blocking=True)
-        W2, lam2, _, _ = cpd.cpd_dgn_solve(Tdev2, dims, R, opts, stream=stream, workspace=ws)
-        Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
-        lh.copy_(lam2, non_blocking=True)
-        e1[i].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+        # per-stage device time: a second K-step region with CUDA-event scopes
+        # around every launch (direct launches; graphs are bypassed while profiling)
+        cpd.cpd_profile_enable(True)
+        ms_prof, _ = _timed_steps(torch, step, flush, stream, args.steps)
+        prof = cpd.cpd_profile_read()
+        cpd.cpd_profile_enable(False)
+
+        # end to end through the C ABI with host buffers: H2D of T, solve, D2H of W and lambda
+        Th = torch.from_numpy(T_flat).pin_memory()
+        Tdev2 = torch.empty_like(Td)
+        n_out = R * sum(dims)
+        Wh = torch.empty(n_out, dtype=torch.float32).pin_memory()
+        lh = torch.empty(R, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            Tdev2.copy_(Th, non_blocking=True)
+            W2, lam2, _, _ = cpd.cpd_dgn_solve(Tdev2, dims, R, opts, stream=stream, workspace=ws)
+            Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
+            lh.copy_(lam2, non_blocking=True)
+        e2e_step()
+        e2e_ms, _ = _timed_steps(torch, e2e_step, flush, stream, args.steps)
     e2e = dict(value=world * args.steps / (e2e_ms * 1e-3), unit=UNIT,
                h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4))
 
@@ -282,14 +289,13 @@ def run_ours(args, rank, world, local_rank):
         return 0
     pk = peaks()
     csum = clk.summary()
-    # dominant stage by total device time in the timed region
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     roof = None
     if dom[0] is not None:
         per = dom[1]["ms"] / dom[1]["launches"]
         roof = algorithmic(dom[0], dims, R, infos[-1], per, pk, csum["sm_mhz"])
         roof.update(kernel=dom[0], launches=dom[1]["launches"], ms_per_launch=per, traffic=None,
-                    peak_source=pk["src"])
+                    peak_source=pk["src"], region="separate profiled K-step region, direct launches")
     stages = {k: dict(ms_per_step=v["ms"] / args.steps, launches_per_step=v["launches"] / args.steps)
               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -298,18 +304,59 @@ def run_ours(args, rank, world, local_rank):
                 config=dict(workload="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4", tensor_dims=list(dims),
                             rank=R, gram_precision=args.gram, refine_maxiter=REFINE_MAXITER,
                             global_batch=world, parallelism=f"independent CPD per GPU x{world}",
-                            l2="flushed between steps (256 MB write)"),
+                            l2="flushed between steps (256 MB write)", launch="cached CUDA graph per solve"),
                 e2e=e2e, gpu_launches=int(launches), roofline=roof, stages=stages,
-                clocks=csum, solve=dict(core_iters=infos[-1]["iters"], core_stop=infos[-1]["stop_name"],
-                                        core_cg=infos[-1]["cg_total"], core_dims=infos[-1]["core_dims"][:3],
-                                        refine_iters=infos[-1]["refine_iters"],
-                                        refine_rel_err=infos[-1]["refine_rel_err"]))
+                profiled_ms_per_step=ms_prof / args.steps,
+                clocks=csum, solve=dict(core_iters=info["iters"], core_stop=info["stop_name"],
+                                        core_cg=info["cg_total"], core_dims=info["core_dims"][:3],
+                                        refine_iters=info["refine_iters"],
+                                        refine_rel_err=info["refine_rel_err"]))
     if not args.no_cpu_baseline:
         Wg = [w.double().cpu().numpy() for w in W]
         lg = lam.double().cpu().numpy()
         cb = cpu_baseline(T, R, Wg, lg, budget_s=args.cpu_budget)
         line["parity"] = cb.pop("parity", None)
         line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush):
+    """Optional line: the 4096-item uneven batch (modes U{8..48}, ranks U{2..8},
+    noise 1e-6) in one persistent launch; CPDs/s of the whole batch."""
+    items = synth.c4_batch()
+    offs, o = [], 0
+    for it in items:
+        offs.append(o)
+        o += it["T"].size
+    flat = np.concatenate([synth.flat(it["T"]).astype(np.float32) for it in items])
+    Tp = torch.from_numpy(flat).to(dev)
+    dims = [list(it["T"].shape) for it in items]
+    ranks = [it["R"] for it in items]
+    opts = cpd.cpd_default_options()
+    ws = torch.empty(cpd.cpd_batch_workspace_size(dims, ranks, opts), dtype=torch.uint8, device=dev)
+
+    def step():
+        return cpd.cpd_batch_solve(Tp, offs, dims, ranks, opts, stream=stream, workspace=ws, want_infos=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        l0 = cpd.cpd_launch_count()
+        with ClockSampler(local_rank) as clk:
+            ms, _ = _timed_steps(torch, step, flush, stream, args.steps)
+        launches = cpd.cpd_launch_count() - l0
+    B = len(items)
+    if rank != 0:
+        return 0
+    line = dict(metric="CPDs/sec (batched uneven CPDs)", value=world * B * args.steps / (ms * 1e-3),
+                unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="batch_4096_uneven_3rd_order_r2-8_noise1e-6", global_batch=B * world,
+                            parallelism=f"one persistent launch per GPU x{world}",
+                            l2="flushed between steps (256 MB write)"),
+                gpu_launches=int(launches), clocks=clk.summary())
     print(json.dumps(line), flush=True)
     return 0
 
@@ -321,6 +368,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gram", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--workload", choices=["compressed", "batch"], default="compressed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -1,7 +1,9 @@
 // C ABI of libcpd: validation, workspace carving and the launch sequence of
 // the method (Fig. "tensorfox-flow" of the thesis).  No allocation happens
 // here; every buffer is the caller's.
+#include <mutex>
 #include <string.h>
+#include <vector>
 
 #include "kernels.h"
 #include "solver.cuh"
@@ -241,6 +243,96 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
   return CPD_OK;
 }
 
+// The launch sequence of one solve (Fig. "tensorfox-flow"), enqueued on st.
+int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, int L, int R,
+                  const float* W0, float* W_out, float* lambda_out, double* trace, cudaStream_t st) {
+  const int trace_cap = trace ? (o.maxiter + o.refine_maxiter) : 0;
+
+  // ---- compression and initial factors -----------------------------------------
+  DgnArgs a{};
+  a.R = R;
+  for (int l = 0; l < CPD_MAX_ORDER; ++l) a.dims[l] = (l < L) ? p.idims[l] : 1;
+  a.init = o.init;
+  a.W0 = W0;
+  if (o.compress) {
+    int rc = run_compress(p, static_cast<const float*>(T), o, st);
+    if (rc != CPD_OK) return rc;
+    a.dev_dims = p.core_dims_dev;
+    a.S = p.core;
+    a.s_f64 = 0;
+    if (o.init == CPD_INIT_GIVEN) {
+      PL("project_given", launch_project_given(L, p.dims, R, p.U, p.core_dims_dev, p.P, W0, p.W0_core, st));
+      a.W0 = p.W0_core;
+    }
+  } else {
+    a.dev_dims = nullptr;
+    a.S = T;
+    a.s_f64 = dtype == CPD_F64;
+  }
+  a.seed = o.seed; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
+  a.maxiter = o.maxiter; a.mu0 = -1.0; a.k0 = 0;
+  a.big_in_smem = p.big_in_smem; a.gscratch = p.gscratch;
+  a.hist = p.hist; a.trace = trace; a.trace_cap = trace_cap; a.trace_slot0 = 0;
+  a.W_out = p.W_core; a.res = p.res;
+  a.cgtab = p.cgtab; a.cgtab_len = p.cgtab_len;
+  int cmax[CPD_MAX_ORDER] = {1, 1, 1, 1};
+  for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
+  Shape sc; make_shape(sc, L, cmax, R);
+  PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
+
+  // ---- uncompression, refinement, output ---------------------------------------------
+  const float* Wfinal = p.W_core;
+  if (o.compress) {
+    PL("uncompress", launch_uncompress(L, p.dims, R, p.U, p.core_dims_dev, p.P, p.W_core, p.W_full, st));
+    Wfinal = p.W_full;
+  }
+  if (o.refine_maxiter > 0) {
+    float* Wr = p.W_full;
+    if (!o.compress) CK(cudaMemcpyAsync(Wr, p.W_core, sizeof(float) * p.n_full, cudaMemcpyDeviceToDevice, st));
+    PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
+    RefinePassArgs pa{};
+    pa.T = static_cast<const float*>(T); pa.L = L; pa.R = R; pa.W = Wr; pa.G = p.rG; pa.esq = p.resq;
+    for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = p.dims[l];
+    pa.done = p.rdone;
+    RefineStepArgs sa{};
+    sa.L = L; sa.R = R; sa.W = Wr; sa.G = p.rG; sa.esq = p.resq; sa.state = p.rstate;
+    for (int l = 0; l < CPD_MAX_ORDER; ++l) sa.dims[l] = p.dims[l];
+    sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = o.refine_maxiter;
+    sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.seed = o.seed; sa.hist = p.rhist;
+    sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
+    sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
+    const int rthreads = 1024;
+    for (int j = 0; j <= o.refine_maxiter; ++j) {
+      pa.want_tsq = (j == 0);
+      PL("refine_pass", launch_refine_pass(pa, st));
+      sa.j = j;
+      PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+    }
+    Wfinal = Wr;
+  }
+  PL("normalize", launch_normalize(L, p.dims, R, Wfinal, W_out, lambda_out, st));
+
+  return CPD_OK;
+}
+
+// ---- CUDA graphs of the launch sequence ----------------------------------------
+// One solve is ~10 + 3 * refine_maxiter launches; replaying a captured graph
+// removes the per-launch host cost.  Graphs are cached per argument set (all
+// pointers, sizes and options), least recently used first out.
+struct GraphKey {
+  int dev, dtype, L, R;
+  long long dims[CPD_MAX_ORDER];
+  cpd_options o;
+  const void* T; const float* W0; float* W_out; float* lam; double* trace; void* ws; size_t ws_bytes;
+};
+struct GraphEntry { GraphKey k; cudaGraphExec_t exec; unsigned long long used; long long kernels; };
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+unsigned long long g_graph_clock = 0;
+constexpr size_t kMaxGraphs = 16;
+
+bool same_key(const GraphKey& a, const GraphKey& b) { return memcmp(&a, &b, sizeof(GraphKey)) == 0; }
+
 }  // namespace
 
 extern "C" {
@@ -312,71 +404,61 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   plan_solve(p, c, o);
   if (!c.ok) return CPD_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
-  const int trace_cap = trace ? (o.maxiter + o.refine_maxiter) : 0;
-
-  // ---- compression and initial factors -----------------------------------------
-  DgnArgs a{};
-  a.R = R;
-  for (int l = 0; l < CPD_MAX_ORDER; ++l) a.dims[l] = (l < L) ? p.idims[l] : 1;
-  a.init = o.init;
-  a.W0 = W0;
-  if (o.compress) {
-    int rc = run_compress(p, static_cast<const float*>(T), o, st);
+  // replay a captured graph of the launch sequence when the stream allows it
+  bool launched = false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (st != nullptr && !profile_enabled() && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
+    GraphKey k;
+    memset(&k, 0, sizeof(k));
+    cudaGetDevice(&k.dev);
+    k.dtype = dtype; k.L = L; k.R = R;
+    for (int l = 0; l < CPD_MAX_ORDER; ++l) k.dims[l] = p.dims[l];
+    k.o = o; k.T = T; k.W0 = W0; k.W_out = W_out; k.lam = lambda_out; k.trace = trace;
+    k.ws = workspace; k.ws_bytes = ws_bytes;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_graph_mu);
+      for (auto& e : g_graphs)
+        if (same_key(e.k, k)) { exec = e.exec; kernels = e.kernels; e.used = ++g_graph_clock; break; }
+    }
+    if (exec == nullptr) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const long long before = cpd_launch_count();
+        const int rc = enqueue_solve(p, o, T, dtype, L, R, W0, W_out, lambda_out, trace, st);
+        kernels = cpd_launch_count() - before;
+        count_launch(-(int)kernels);     // captured, not launched: counted when replayed
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (rc == CPD_OK && ec == cudaSuccess && g != nullptr &&
+            cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+          std::lock_guard<std::mutex> lk(g_graph_mu);
+          if (g_graphs.size() >= kMaxGraphs) {
+            size_t victim = 0;
+            for (size_t i = 1; i < g_graphs.size(); ++i)
+              if (g_graphs[i].used < g_graphs[victim].used) victim = i;
+            cudaGraphExecDestroy(g_graphs[victim].exec);
+            g_graphs.erase(g_graphs.begin() + victim);
+          }
+          g_graphs.push_back(GraphEntry{k, exec, ++g_graph_clock, kernels});
+        } else {
+          exec = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();          // a failed capture falls back to direct launches
+      }
+    }
+    if (exec != nullptr) {
+      if (cudaGraphLaunch(exec, st) != cudaSuccess) return CPD_ERR_CUDA;
+      count_launch((int)kernels);      // the kernels the graph replays
+      launched = true;
+    }
+  }
+  if (!launched) {
+    const int rc = enqueue_solve(p, o, T, dtype, L, R, W0, W_out, lambda_out, trace, st);
     if (rc != CPD_OK) return rc;
-    a.dev_dims = p.core_dims_dev;
-    a.S = p.core;
-    a.s_f64 = 0;
-    if (o.init == CPD_INIT_GIVEN) {
-      PL("project_given", launch_project_given(L, p.dims, R, p.U, p.core_dims_dev, p.P, W0, p.W0_core, st));
-      a.W0 = p.W0_core;
-    }
-  } else {
-    a.dev_dims = nullptr;
-    a.S = T;
-    a.s_f64 = dtype == CPD_F64;
   }
-  a.seed = o.seed; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
-  a.maxiter = o.maxiter; a.mu0 = -1.0; a.k0 = 0;
-  a.big_in_smem = p.big_in_smem; a.gscratch = p.gscratch;
-  a.hist = p.hist; a.trace = trace; a.trace_cap = trace_cap; a.trace_slot0 = 0;
-  a.W_out = p.W_core; a.res = p.res;
-  a.cgtab = p.cgtab; a.cgtab_len = p.cgtab_len;
-  int cmax[CPD_MAX_ORDER] = {1, 1, 1, 1};
-  for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
-  Shape sc; make_shape(sc, L, cmax, R);
-  PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
-
-  // ---- uncompression, refinement, output ---------------------------------------------
-  const float* Wfinal = p.W_core;
-  if (o.compress) {
-    PL("uncompress", launch_uncompress(L, p.dims, R, p.U, p.core_dims_dev, p.P, p.W_core, p.W_full, st));
-    Wfinal = p.W_full;
-  }
-  if (o.refine_maxiter > 0) {
-    float* Wr = p.W_full;
-    if (!o.compress) CK(cudaMemcpyAsync(Wr, p.W_core, sizeof(float) * p.n_full, cudaMemcpyDeviceToDevice, st));
-    PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
-    RefinePassArgs pa{};
-    pa.T = static_cast<const float*>(T); pa.L = L; pa.R = R; pa.W = Wr; pa.G = p.rG; pa.esq = p.resq;
-    for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = p.dims[l];
-    pa.done = p.rdone;
-    RefineStepArgs sa{};
-    sa.L = L; sa.R = R; sa.W = Wr; sa.G = p.rG; sa.esq = p.resq; sa.state = p.rstate;
-    for (int l = 0; l < CPD_MAX_ORDER; ++l) sa.dims[l] = p.dims[l];
-    sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = o.refine_maxiter;
-    sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.seed = o.seed; sa.hist = p.rhist;
-    sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
-    sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
-    const int rthreads = 1024;
-    for (int j = 0; j <= o.refine_maxiter; ++j) {
-      pa.want_tsq = (j == 0);
-      PL("refine_pass", launch_refine_pass(pa, st));
-      sa.j = j;
-      PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
-    }
-    Wfinal = Wr;
-  }
-  PL("normalize", launch_normalize(L, p.dims, R, Wfinal, W_out, lambda_out, st));
 
   if (info) {
     DevResult hr;

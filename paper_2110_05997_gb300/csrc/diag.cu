@@ -17,6 +17,7 @@ static std::vector<Rec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
 
 void count_launch(int n) { g_launches += n; }
+bool profile_enabled() { return g_prof; }
 
 static cudaEvent_t take_event() {
   if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }

@@ -17,6 +17,7 @@ struct Dims4 { long long v[CPD_MAX_ORDER]; };
 // Diagnostics (diag.cu): every kernel launch is counted; while profiling is
 // enabled a ProfScope records a CUDA event pair around its launches.
 void count_launch(int n = 1);
+bool profile_enabled();
 struct ProfScope {
   ProfScope(cudaStream_t st, const char* name);
   ~ProfScope();
