@@ -73,7 +73,8 @@ typedef enum {
 /* Arithmetic of the compression Gram matrices. */
 typedef enum {
   CPD_GRAM_FP32 = 0,    /* FP32 CUDA-core Gram                                   */
-  CPD_GRAM_BF16 = 1     /* BF16 tcgen05 tensor-core Gram, FP32 accumulate (mode 1);
+  CPD_GRAM_BF16 = 1     /* BF16 tcgen05 tensor-core Gram, FP32 accumulate (mode 1,
+                           I_1 <= 256, T 16-byte aligned, else CPD_ERR_UNSUPPORTED);
                            accuracy is won back by refinement in the original space */
 } cpd_gram_precision;
 
@@ -231,7 +232,8 @@ int cpd_jtj_apply(int L, const int64_t* dims, int R, const float* W, const float
 /*
  * cpd_mode_gram — G = T_(l) T_(l)^T (I_l x I_l, FP32, column-major), the Gram
  * route to the left singular vectors of the unfolding (App. A).  precision is
- * a cpd_gram_precision (BF16 supported for mode l = 0 only).
+ * a cpd_gram_precision (BF16 supported for mode l = 0 with I_1 <= 256 and a
+ * 16-byte-aligned T only; otherwise CPD_ERR_UNSUPPORTED).
  */
 int cpd_mode_gram(const float* T, int L, const int64_t* dims, int mode, int precision,
                   float* G_out, void* workspace, size_t ws_bytes, void* stream);

@@ -397,6 +397,8 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   if (o.init == CPD_INIT_GIVEN && W0 == nullptr) return CPD_ERR_INVALID_ARG;
   if (dtype == CPD_F64 && (o.compress || o.refine_maxiter > 0)) return CPD_ERR_UNSUPPORTED;
   if (o.gram_precision == CPD_GRAM_BF16 && !o.compress) return CPD_ERR_INVALID_ARG;
+  if (o.gram_precision == CPD_GRAM_BF16 && !gram_bf16_tc_supported(dims[0], static_cast<const float*>(T)))
+    return CPD_ERR_UNSUPPORTED;
   if (o.refine_maxiter > 0 && !refine_pass_supported((int)dims[0], R)) return CPD_ERR_UNSUPPORTED;
 
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
@@ -498,6 +500,7 @@ int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_op
   cpd_options o; cpd_default_options(&o);
   if (opts) o = *opts;
   o.compress = 1; o.refine_maxiter = 0;
+  if (o.gram_precision == CPD_GRAM_BF16 && !gram_bf16_tc_supported(dims[0], T)) return CPD_ERR_UNSUPPORTED;
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = CPD_F32;
   Carver c(workspace, ws_bytes);
   plan_solve(p, c, o);
@@ -567,7 +570,7 @@ int cpd_mode_gram(const float* T, int L, const int64_t* dims, int mode, int prec
   if (v != CPD_OK) return v;
   if (!T || !G_out || mode < 0 || mode >= L) return CPD_ERR_INVALID_ARG;
   if (precision != CPD_GRAM_FP32 && precision != CPD_GRAM_BF16) return CPD_ERR_INVALID_ARG;
-  if (precision == CPD_GRAM_BF16 && mode != 0) return CPD_ERR_UNSUPPORTED;
+  if (precision == CPD_GRAM_BF16 && (mode != 0 || !gram_bf16_tc_supported(dims[0], T))) return CPD_ERR_UNSUPPORTED;
   long long a = 1, c = 1;
   for (int j = 0; j < mode; ++j) a *= dims[j];
   for (int j = mode + 1; j < L; ++j) c *= dims[j];

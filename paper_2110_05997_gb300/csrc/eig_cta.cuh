@@ -3,8 +3,8 @@
 // matrix), and the truncation rank of Algorithm "Compression" (Sec. 4.1.1).
 // Subspace iteration (FP32 products, Cholesky-QR orthonormalisation) and a
 // Rayleigh-Ritz step whose small symmetric eigenproblem is solved by cyclic
-// Jacobi in FP64.  Shared by the single-tensor eigen kernel and the batched
-// solver.
+// Jacobi (FP32 sweeps, then an FP64 polish).  Shared by the single-tensor
+// eigen kernel and the batched solver.
 #pragma once
 
 #include "kernels.h"
@@ -23,77 +23,218 @@ __host__ __device__ inline int eig_m(int I, int P) {
 }
 
 
-// Cyclic Jacobi with a round-robin parallel ordering on the m x m symmetric H
-// (Golub & Van Loan, Algorithm "cyclic Jacobi" with the 2x2 symmetric Schur
-// rotation); V accumulates the rotations.  FP64 throughout: H is the small
-// Rayleigh-Ritz matrix (m <= P + 6), whose eigenvalues span the signal and the
-// noise floor; FP32 rotations lose ~1e-5 of the signal subspace there.
-static __device__ void jacobi_eig(double* H, double* V, int m, double* red) {
-  __shared__ double cs[kMaxM], sn[kMaxM];
-  __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1];
-  __shared__ double s_off, s_diag;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) V[e] = (e % (m + 1) == 0) ? 1.0 : 0.0;
+// The 2x2 symmetric Schur rotation (c, s) that zeroes h_pq (Golub & Van Loan,
+// "symmetric Schur decomposition"); identity (returns false) when q is the
+// padding index or |h_pq| <= skip * (|h_pp| + |h_qq|).  The tangent is formed
+// in FP32 (the rotation only has to reduce h_pq) from the difference
+// h_qq - h_pp taken in the working precision, and (c, s) is renormalised by
+// one Newton step for 1/sqrt(c^2 + s^2) in the working precision, so that the
+// rotation is orthogonal to that precision.
+template <typename Real>
+__device__ __forceinline__ bool jacobi_rot(const Real* H, int m, int p, int q, float skip, Real& c, Real& s) {
+  c = 1; s = 0;
+  if (q >= m) return false;
+  const Real hpq = H[p * m + q], hpp = H[p * m + p], hqq = H[q * m + q];
+  const float apq = (float)hpq;
+  if (!(fabsf(apq) > 1e-35f) || !(fabs(hpq) > (Real)skip * (fabs(hpp) + fabs(hqq)))) return false;
+  const float tau = __fdividef((float)(hqq - hpp), 2.f * apq);
+  float tt;
+  if (fabsf(tau) > 1e18f) {
+    tt = __fdividef(0.5f, tau);
+  } else {
+    const float r = fmaf(tau, tau, 1.f);
+    tt = copysignf(__fdividef(1.f, fabsf(tau) + r * rsqrtf(r)), tau);
+  }
+  const float c0 = rsqrtf(fmaf(tt, tt, 1.f)), s0 = tt * c0;
+  if (sizeof(Real) == sizeof(double)) {
+    const double cd = (double)c0, sd = (double)s0;
+    const double kf = fma(-0.5, fma(cd, cd, sd * sd), 1.5);
+    c = (Real)(cd * kf); s = (Real)(sd * kf);
+  } else {
+    const float kf = fmaf(-0.5f, fmaf(c0, c0, s0 * s0), 1.5f);
+    c = (Real)(c0 * kf); s = (Real)(s0 * kf);
+  }
+  return true;
+}
+
+// One cyclic sweep of Jacobi with the round-robin parallel ordering (Golub &
+// Van Loan, "parallel Jacobi") on the m x m symmetric H (row-major); V
+// accumulates the rotations.  Per round: one thread per pair forms its
+// rotation; then the round's m/2 disjoint rotations J are applied as
+// H <- J^T H J into the other buffer, one 2x2 block (pair k1 rows, pair k2
+// columns) per work item, and V <- V J in place, one (row, pair) per item.
+// H and Hn swap roles after each round.
+template <typename Real>
+static __device__ void jacobi_sweep(Real*& H, Real*& Hn, Real* V, int m, float skip) {
+  __shared__ Real r_c[kMaxM / 2], r_s[kMaxM / 2];
+  __shared__ int r_p[kMaxM / 2], r_q[kMaxM / 2];
+  __shared__ bool r_act[kMaxM / 2];
+  const int me = m + (m & 1), np = me / 2, nr = me - 1;
+  const int nblk = np * np;
+  // integer quotients of the work-item index by np and m through FP32
+  // reciprocals: exact here, as (e + 0.5) / np stays 0.5 / np away from an
+  // integer and e < 2^12
+  const float inv_np = 1.f / (float)np, inv_m = 1.f / (float)m;
+  for (int t = 0; t < nr; ++t) {
+    if (threadIdx.x < np) {
+      const int k = threadIdx.x;
+      int p = 0, q = t + 1;
+      if (k != 0) {
+        int x = t + k, y = t - k + nr;
+        if (x >= nr) x -= nr;
+        if (y >= nr) y -= nr;
+        p = x + 1; q = y + 1;
+      }
+      if (p > q) { const int x = p; p = q; q = x; }
+      Real c, s;
+      r_act[k] = jacobi_rot(H, m, p, q, skip, c, s);
+      r_p[k] = p; r_q[k] = q; r_c[k] = c; r_s[k] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nblk + np * m; e += blockDim.x) {
+      if (e < nblk) {
+        const int k1 = __float2int_rd(((float)e + 0.5f) * inv_np), k2 = e - k1 * np;
+        const int p1 = r_p[k1], q1 = r_q[k1], p2 = r_p[k2], q2 = r_q[k2];
+        const bool r1 = q1 < m, r2 = q2 < m;
+        const Real a = H[p1 * m + p2];
+        const Real b = r2 ? H[p1 * m + q2] : (Real)0;
+        const Real cc = r1 ? H[q1 * m + p2] : (Real)0;
+        const Real d = (r1 && r2) ? H[q1 * m + q2] : (Real)0;
+        Real o00 = a, o01 = b, o10 = cc, o11 = d;
+        if (r_act[k1]) {                                  // rows
+          const Real c1 = r_c[k1], s1 = r_s[k1];
+          o00 = c1 * a - s1 * cc; o01 = c1 * b - s1 * d;
+          o10 = s1 * a + c1 * cc; o11 = s1 * b + c1 * d;
+        }
+        if (r_act[k2]) {                                  // columns
+          const Real c2 = r_c[k2], s2 = r_s[k2];
+          const Real x0 = o00, x1 = o10;
+          o00 = c2 * x0 - s2 * o01; o01 = s2 * x0 + c2 * o01;
+          o10 = c2 * x1 - s2 * o11; o11 = s2 * x1 + c2 * o11;
+        }
+        Hn[p1 * m + p2] = o00;
+        if (r2) Hn[p1 * m + q2] = o01;
+        if (r1) Hn[q1 * m + p2] = o10;
+        if (r1 && r2) Hn[q1 * m + q2] = o11;
+      } else {
+        const int f = e - nblk, k = __float2int_rd(((float)f + 0.5f) * inv_m), i = f - k * m;
+        if (!r_act[k]) continue;
+        const int p = r_p[k], q = r_q[k];
+        const Real c = r_c[k], s = r_s[k];
+        const Real vp = V[i * m + p], vq = V[i * m + q];
+        V[i * m + p] = c * vp - s * vq;
+        V[i * m + q] = s * vp + c * vq;
+      }
+    }
+    __syncthreads();
+    Real* x = H; H = Hn; Hn = x;
+  }
+}
+
+// Off-diagonal and diagonal squared masses of H (warp 0, FP32 partial sums of
+// the working-precision squares), broadcast through shared memory.
+template <typename Real>
+static __device__ void jacobi_masses(const Real* H, int m, float& off, float& diag) {
+  __shared__ float s_off, s_diag;
+  if (threadIdx.x < 32) {
+    float o = 0.f, d = 0.f;
+    for (int e = threadIdx.x; e < m * m; e += 32) {
+      const int r = e / m, c2 = e - r * m;
+      const float h = (float)H[e];
+      if (r == c2) d = fmaf(h, h, d); else o = fmaf(h, h, o);
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) { o += __shfl_xor_sync(0xffffffffu, o, k); d += __shfl_xor_sync(0xffffffffu, d, k); }
+    if (threadIdx.x == 0) { s_off = o; s_diag = d; }
+  }
   __syncthreads();
-  const int me = m + (m & 1), np = me / 2;
-  for (int sweep = 0; sweep < 20; ++sweep) {
+  off = s_off; diag = s_diag;
+  __syncthreads();
+}
+
+// Y = op(A) * B for m x m row-major FP64 matrices, op(A) = A or A^T; when
+// `ns` is set, Y = 1.5 I - 0.5 A^T B instead (the Newton-Schulz factor).
+static __device__ void small_gemm(const double* A, bool at, const double* B, double* Y, int m, bool ns) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    for (; k + 1 < m; k += 2) {
+      s0 = fma(at ? A[k * m + i] : A[i * m + k], B[k * m + j], s0);
+      s1 = fma(at ? A[(k + 1) * m + i] : A[i * m + k + 1], B[(k + 1) * m + j], s1);
+    }
+    if (k < m) s0 = fma(at ? A[k * m + i] : A[i * m + k], B[k * m + j], s0);
+    const double s = s0 + s1;
+    Y[e] = ns ? ((i == j ? 1.5 : 0.0) - 0.5 * s) : s;
+  }
+  __syncthreads();
+}
+
+// Eigen-decomposition H = V diag(h) V^T of the m x m symmetric Rayleigh-Ritz
+// (or small Gram) matrix, to FP64 accuracy.  H's eigenvalues span the signal
+// and the noise floor, so an FP32-only decomposition loses ~1e-5 of the signal
+// subspace; FP64 rotations throughout are bound by the FP64 pipe.  Three
+// stages instead:
+//   1. cyclic Jacobi in FP32 on a copy of H until the off-diagonal mass stops
+//      falling (it ends at FP32 rounding level, ~1e-7 relative);
+//   2. the FP32 eigenvectors V0 made orthonormal to FP64 precision by two
+//      Newton-Schulz steps X <- X (3I - X^T X) / 2 (Higham, "Functions of
+//      Matrices", the Newton-Schulz iteration for the polar factor), and
+//      H <- V1^T H V1, now diagonal up to ~1e-7 relative;
+//   3. FP64 cyclic Jacobi sweeps on that H accumulating into V1; rotations
+//      below FP64 resolution are skipped, so the sweeps after the first only
+//      work inside clusters of close eigenvalues.
+// W1, W2: m x m FP64 scratch each.  On return H is diagonal (the eigenvalues)
+// and the columns of V are the eigenvectors.
+static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, double* W2) {
+  float* Hf = reinterpret_cast<float*>(W1);
+  float* Vf = Hf + m * m;
+  float* Hf2 = reinterpret_cast<float*>(W2);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    Hf[e] = (float)H[e];
+    Vf[e] = (e % (m + 1) == 0) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  float off, diag, prev = 3.4e38f;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    jacobi_masses(Hf, m, off, diag);
+    if (!(off > 1e-13f * diag) || diag == 0.f) break;
+    if (off <= 1e-9f * diag && off > 0.25f * prev) break;      // at FP32 rounding level
+    prev = off;
+    jacobi_sweep<float>(Hf, Hf2, Vf, m, 0.f);
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) V[e] = (double)Vf[e];
+  __syncthreads();
+  small_gemm(V, true, V, W2, m, true);          // W2 = (3I - V0^T V0) / 2
+  small_gemm(V, false, W2, W1, m, false);       // W1 = V0 W2
+  small_gemm(W1, true, W1, W2, m, true);        // second step: W2 = (3I - W1^T W1) / 2
+  small_gemm(W1, false, W2, V, m, false);       // V = V1 = W1 W2
+  small_gemm(H, false, V, W2, m, false);        // W2 = H V1
+  small_gemm(V, true, W2, H, m, false);         // H = V1^T H V1
+  double* Hc = H;
+  double* Hn = W1;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    __shared__ double s_o, s_d;
     if (threadIdx.x < 32) {
+      // masses in FP64 (the stop test is far below FP32 rounding)
       double o = 0.0, d = 0.0;
       for (int e = threadIdx.x; e < m * m; e += 32) {
         const int r = e / m, c2 = e - r * m;
-        if (r == c2) d = fma(H[e], H[e], d); else o = fma(H[e], H[e], o);
+        if (r == c2) d = fma(Hc[e], Hc[e], d); else o = fma(Hc[e], Hc[e], o);
       }
 #pragma unroll
       for (int k = 16; k > 0; k >>= 1) { o += __shfl_xor_sync(0xffffffffu, o, k); d += __shfl_xor_sync(0xffffffffu, d, k); }
-      if (threadIdx.x == 0) { s_off = o; s_diag = d; }
+      if (threadIdx.x == 0) { s_o = o; s_d = d; }
     }
     __syncthreads();
-    if (s_off <= 1e-26 * s_diag || s_diag == 0.0) break;
-    for (int t = 0; t < me - 1; ++t) {
-      if (threadIdx.x < np) {
-        const int k = threadIdx.x;
-        int p, q;
-        if (k == 0) { p = 0; q = (t % (me - 1)) + 1; }
-        else { p = ((t + k) % (me - 1)) + 1; q = ((t - k + me - 1) % (me - 1)) + 1; }
-        if (p > q) { const int x = p; p = q; q = x; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          // tangent of the Schur rotation in FP32 (it only has to reduce H_pq),
-          // then (c, s) renormalised in FP64 by one Newton step for
-          // 1/sqrt(c^2 + s^2), so the rotation is orthogonal to FP64 precision.
-          const float apq = (float)H[p * m + q];
-          if (fabsf(apq) > 1e-35f) {
-            const float tau = ((float)H[q * m + q] - (float)H[p * m + p]) / (2.f * apq);
-            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-            const float c0 = rsqrtf(fmaf(tt, tt, 1.f));
-            const double cd = (double)c0, sd = (double)(tt * c0);
-            const double nrm = fma(cd, cd, sd * sd);
-            const double kf = fma(-0.5, nrm, 1.5);
-            c = cd * kf; s = sd * kf;
-          }
-        } else { p = q = -1; }
-        pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < np * m; e += blockDim.x) {     // rows: J^T H
-        const int k = e / m, j = e - k * m, p = pp[k], q = qq[k];
-        if (p < 0) continue;
-        const double hp = H[p * m + j], hq = H[q * m + j];
-        H[p * m + j] = cs[k] * hp - sn[k] * hq;
-        H[q * m + j] = sn[k] * hp + cs[k] * hq;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < np * m; e += blockDim.x) {     // columns: H J, V J
-        const int k = e / m, i = e - k * m, p = pp[k], q = qq[k];
-        if (p < 0) continue;
-        const double hp = H[i * m + p], hq = H[i * m + q];
-        H[i * m + p] = cs[k] * hp - sn[k] * hq;
-        H[i * m + q] = sn[k] * hp + cs[k] * hq;
-        const double vp = V[i * m + p], vq = V[i * m + q];
-        V[i * m + p] = cs[k] * vp - sn[k] * vq;
-        V[i * m + q] = sn[k] * vp + cs[k] * vq;
-      }
-      __syncthreads();
-    }
+    const double o = s_o, d = s_d;
+    __syncthreads();
+    if (o <= 1e-26 * d || d == 0.0) break;
+    jacobi_sweep<double>(Hc, Hn, V, m, 1e-17f);
+  }
+  if (Hc != H) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) H[e] = Hc[e];
+    __syncthreads();
   }
 }
 
@@ -182,25 +323,38 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
 }
 
 // Z = G Q (G symmetric I x I, column-major; Q I x m): a thread computes four
-// columns of one row with independent accumulators.
+// columns of two rows (i and i + ceil(I/2)) with independent accumulators, so
+// each broadcast load of Q feeds two FMAs (shared-memory wavefronts, not FMAs,
+// bound this product).
 static __device__ void gram_times(const float* G, const float* Q, float* Z, int I, int m) {
-  const int mq = (m + 3) >> 2;
-  for (int e = threadIdx.x; e < I * mq; e += blockDim.x) {
-    const int i = e % I, j0 = (e / I) * 4;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  const int mq = (m + 3) >> 2, Ih = (I + 1) >> 1;
+  for (int e = threadIdx.x; e < Ih * mq; e += blockDim.x) {
+    const int i = e % Ih, j0 = (e / Ih) * 4, i2 = i + Ih;
+    const bool two = i2 < I;
+    const int i2c = two ? i2 : i;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
     const float* q0 = Q + (size_t)j0 * I;
     const bool h1 = j0 + 1 < m, h2 = j0 + 2 < m, h3 = j0 + 3 < m;
+    const float* q1 = h1 ? q0 + I : q0;
+    const float* q2 = h2 ? q0 + 2 * I : q0;
+    const float* q3 = h3 ? q0 + 3 * I : q0;
+#pragma unroll 4
     for (int k = 0; k < I; ++k) {
-      const float g = G[i + (size_t)I * k];
-      a0 = fmaf(g, q0[k], a0);
-      if (h1) a1 = fmaf(g, q0[I + k], a1);
-      if (h2) a2 = fmaf(g, q0[2 * I + k], a2);
-      if (h3) a3 = fmaf(g, q0[3 * I + k], a3);
+      const float g = G[i + (size_t)I * k], g2 = G[i2c + (size_t)I * k];
+      const float x0 = q0[k], x1 = q1[k], x2 = q2[k], x3 = q3[k];
+      a0 = fmaf(g, x0, a0); a1 = fmaf(g, x1, a1); a2 = fmaf(g, x2, a2); a3 = fmaf(g, x3, a3);
+      b0 = fmaf(g2, x0, b0); b1 = fmaf(g2, x1, b1); b2 = fmaf(g2, x2, b2); b3 = fmaf(g2, x3, b3);
     }
     Z[(size_t)j0 * I + i] = a0;
     if (h1) Z[(size_t)(j0 + 1) * I + i] = a1;
     if (h2) Z[(size_t)(j0 + 2) * I + i] = a2;
     if (h3) Z[(size_t)(j0 + 3) * I + i] = a3;
+    if (two) {
+      Z[(size_t)j0 * I + i2] = b0;
+      if (h1) Z[(size_t)(j0 + 1) * I + i2] = b1;
+      if (h2) Z[(size_t)(j0 + 2) * I + i2] = b2;
+      if (h3) Z[(size_t)(j0 + 3) * I + i2] = b3;
+    }
   }
   __syncthreads();
 }
@@ -225,7 +379,7 @@ static __device__ void rayleigh(const float* Q, const float* Z, double* H, int I
 
 __host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g) {
   const int m = eig_m(I, P);
-  size_t base = 128 * sizeof(double) + 2 * (size_t)m * m * sizeof(double) + (size_t)m * m * sizeof(float) +
+  size_t base = 128 * sizeof(double) + 4 * (size_t)m * m * sizeof(double) + (size_t)m * m * sizeof(float) +
                 (size_t)((m + 3) & ~3) * sizeof(float) + 2 * (size_t)I * m * sizeof(float);
   return with_g ? base + (size_t)I * I * sizeof(float) : base;
 }
@@ -236,11 +390,13 @@ __host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g) {
 // that workspace first (it fits); otherwise G is read where it is.
 static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
   const int I = a.I, P = a.P, m = eig_m(I, P);
-  // layout: red(128 d) | H(m*m d) | V(m*m d) | Lf(m*m) | Cf(m) | Q(I*m) | Z(I*m) | G(I*I if it fits)
+  // layout: red(128 d) | H, V, W1, W2 (m*m d each) | Lf(m*m) | Cf(m) | Q(I*m) | Z(I*m) | G(I*I if it fits)
   double* red = reinterpret_cast<double*>(smem_raw);
   double* H = red + 128;
   double* V = H + m * m;
-  float* Lf = reinterpret_cast<float*>(V + m * m);
+  double* W1 = V + m * m;
+  double* W2 = W1 + m * m;
+  float* Lf = reinterpret_cast<float*>(W2 + m * m);
   float* Cf = Lf + m * m;
   float* Q = Cf + ((m + 3) & ~3);
   float* Z = Q + (size_t)I * m;
@@ -258,7 +414,7 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     // the whole space: Jacobi on G itself (m = I <= P + 6)
     for (int e = threadIdx.x; e < I * I; e += blockDim.x) H[e] = (double)G[e];
     __syncthreads();
-    jacobi_eig(H, V, I, red);
+    jacobi_eig(H, V, I, W1, W2);
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) {
       const int j = e / I, i = e - j * I;
       Q[j * I + i] = (float)V[i * m + j];
@@ -287,7 +443,7 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     }
     // Rayleigh-Ritz: H = Q^T G Q, eig, U = Q V
     rayleigh(Q, Z, H, I, m);
-    jacobi_eig(H, V, m, red);
+    jacobi_eig(H, V, m, W1, W2);
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) {
       const int j = e / I, i = e - j * I;
       float s = 0.f;

@@ -90,6 +90,7 @@ cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G,
 cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float* G, float* scratch,
                                 size_t scratch_bytes, cudaStream_t st);
 size_t gram_bf16_tc_scratch_bytes(long long I, long long C);
+bool gram_bf16_tc_supported(long long I, const float* T);
 struct EigArgs {
   const float* G;             // I x I
   int I, P;                   // P = min(I, R) leading eigenpairs
