@@ -3,9 +3,10 @@
 
 Workload (one step = one whole CPD through the C ABI): a 200x200x200 FP32
 tensor of rank 10 with pairwise factor collinearity 0.5 and relative noise
-1e-4 (synthetic, seeded), compressed by ST-MLSVD to a <= 10x10x10 core, dGN on
-the core from the MLSVD-energy start, uncompression and refinement
-iterations on T, output normalisation.  Metric: CPDs per second, with the
+1e-4 (synthetic, seeded), compressed by ST-MLSVD to a <= 10x10x10 core (the
+first-mode Gram on BF16 tensor cores by default, --gram fp32 for CUDA cores),
+dGN on the core from the MLSVD-energy start, uncompression and FP32
+refinement iterations on T, output normalisation.  Metric: CPDs per second, with the
 fit of every result checked against the FP64 oracle's (within 1e-6).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -367,7 +368,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--gram", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--gram", choices=["fp32", "bf16"], default="bf16")
     ap.add_argument("--workload", choices=["compressed", "batch"], default="compressed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -5,23 +5,30 @@
 // of 64*I floats.
 //
 // One CTA per SM takes a contiguous range of 64-column steps:
-//   * thread 0 streams each step's FP32 block into a shared-memory stage with a
-//     bulk asynchronous copy completed on an mbarrier (several stages in flight);
-//   * the warpgroup converts the stage to BF16, writing it K-major (row i holds
+//   * an issuer thread (warp 8) streams each step's FP32 block into a
+//     shared-memory stage with a bulk asynchronous copy completed on an
+//     mbarrier (several stages in flight);
+//   * eight warps convert the stage to BF16, writing it K-major (row i holds
 //     the step's 64 values of row i of A, 128 bytes) in the 128-byte-swizzled
 //     layout the tensor core reads;
-//   * thread 0 issues tcgen05.mma (M = 128, N = ceil16(I), K = 16 each) into
+//   * the issuer issues tcgen05.mma (M = 128, N = ceil16(I), K = 16 each) into
 //     FP32 accumulators in tensor memory: D_m += X[128m : 128m+128] X^T for the
 //     one or two 128-row tiles m of X, and commits to an mbarrier that frees
 //     the BF16 buffer (double-buffered) for the step after next;
-//   * finally each thread reads its accumulator row back (tcgen05.ld) and adds
-//     it into G with vector atomics; G is symmetric, so row i of D goes to the
-//     contiguous column i of G.
+//   * finally warps 0-3 read the accumulator rows back (tcgen05.ld) into
+//     shared memory, the CTAs of a thread-block cluster sum their partial
+//     Grams through distributed shared memory (each CTA a slice of rows), and
+//     add the sums into G with vector atomics; G is symmetric, so row i of D
+//     goes to the contiguous column i of G.
 // Every mbarrier wait is bounded; on a timeout the CTA poisons G with NaN
 // (the solve then ends with a numeric status), waits a bounded time for its
 // own copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.h"
 
@@ -29,9 +36,12 @@ namespace cpdk {
 namespace {
 
 constexpr int kKT = 64;                   // unfolding columns per step
-constexpr int kThreads = 128;             // one warpgroup
+constexpr int kConv = 256;                // converting threads (warps 0-7; warps 0-3 read tensor memory back)
+constexpr int kIssuer = 256;              // thread issuing the bulk copies and the MMAs (warp 8)
+constexpr int kThreads = kConv + 32;
 constexpr int kMaxStages = 4;
 constexpr int kSpinLimit = 1 << 21;       // bounded mbarrier polling
+constexpr int kCluster = 8;               // CTAs whose partial Grams are summed on chip
 
 struct TcArgs {
   const float* A;       // I x C column-major
@@ -80,13 +90,22 @@ __host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Eight FP32 values -> eight BF16 (round to nearest even), packed in order.
+__device__ __forceinline__ uint4 pack_bf16x8(const float (&f)[8]) {
+  uint4 w;
+  __nv_bfloat162 h0 = __floats2bfloat162_rn(f[0], f[1]), h1 = __floats2bfloat162_rn(f[2], f[3]);
+  __nv_bfloat162 h2 = __floats2bfloat162_rn(f[4], f[5]), h3 = __floats2bfloat162_rn(f[6], f[7]);
+  w.x = *reinterpret_cast<uint32_t*>(&h0); w.y = *reinterpret_cast<uint32_t*>(&h1);
+  w.z = *reinterpret_cast<uint32_t*>(&h2); w.w = *reinterpret_cast<uint32_t*>(&h3);
+  return w;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long k_begin = (long long)blockIdx.x * a.nk / gridDim.x;
   const long long k_end = (long long)(blockIdx.x + 1) * a.nk / gridDim.x;
-  const int nsteps = (int)(k_end - k_begin);
-  if (nsteps <= 0) return;
+  const int nsteps = (int)(k_end - k_begin);      // >= 1 when gridDim.x <= nk
 
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -134,8 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
         "l"(src), "r"(st_bytes), "r"(bar)
         : "memory");
   };
-  int issued = 0;                      // steps whose copy has been issued
-  if (tid == 0) {
+  int issued = 0;                      // steps whose copy has been issued (issuer thread)
+  if (tid == kIssuer) {
     for (int j = 0; j < S && j < nsteps; ++j) {
       if (k_begin + j >= a.nk_full) break;
       issue(j);
@@ -160,30 +179,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
     unsigned char* bf = sm + o_bf + (uint32_t)b * bf_bytes;
     const float* stg = reinterpret_cast<const float*>(sm + o_st + (uint32_t)s * st_bytes);
     const int cols = tail ? (int)(a.C - k * kKT) : kKT;
-    for (int q = tid; q < I * 8; q += kThreads) {
-      const int c = q / I, i = q - c * I;
-      float v[8];
-      if (!tail) {
+    if (!tail && (I & 3) == 0) {
+      // item (g, c): rows 4g..4g+3, values 8c..8c+7 of the step, read as
+      // float4 along the rows.  Items go to threads by diagonals of 8 x 8
+      // blocks: in quarter-warp t of block b, lane k takes c = k and
+      // g = 8b + (k + t) % 8, so that (with I % 4 == 0) the eight lanes of
+      // every quarter-warp hit eight different 16-byte bank groups both in
+      // the loads and in the swizzled stores.
+      const float4* stg4 = reinterpret_cast<const float4*>(stg);
+      const int I4 = I >> 2, nb = (I4 + 7) >> 3;
+      for (int e = tid; tid < kConv && e < nb * 64; e += kConv) {
+        const int k = e & 7, t = (e >> 3) & 7, bb = e >> 6;
+        const int c = k, g = 8 * bb + ((k + t) & 7);
+        if (g >= I4) continue;
+        float4 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = stg[(c * 8 + u) * I + i];
-      } else {
+        for (int u = 0; u < 8; ++u) v[u] = stg4[(c * 8 + u) * I4 + g];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          v[u] = (c * 8 + u < cols) ? a.A[((size_t)k * kKT + c * 8 + u) * (size_t)I + i] : 0.f;
+        for (int x = 0; x < 4; ++x) {
+          const int i = 4 * g + x, r = i & 7;
+          float f[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) f[u] = x == 0 ? v[u].x : x == 1 ? v[u].y : x == 2 ? v[u].z : v[u].w;
+          *reinterpret_cast<uint4*>(bf + (i >> 3) * 1024 + r * 128 + ((c ^ r) << 4)) = pack_bf16x8(f);
+        }
       }
-      uint4 w;
-      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
-      w.x = *reinterpret_cast<uint32_t*>(&h0); w.y = *reinterpret_cast<uint32_t*>(&h1);
-      w.z = *reinterpret_cast<uint32_t*>(&h2); w.w = *reinterpret_cast<uint32_t*>(&h3);
-      const int r = i & 7;
-      *reinterpret_cast<uint4*>(bf + (i >> 3) * 1024 + r * 128 + ((c ^ r) << 4)) = w;
+    } else {
+      for (int c = 0; c < 8; ++c) {
+        for (int i = tid; tid < kConv && i < I; i += kConv) {
+          float f[8];
+          if (!tail) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) f[u] = stg[(c * 8 + u) * I + i];
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              f[u] = (c * 8 + u < cols) ? a.A[((size_t)k * kKT + c * 8 + u) * (size_t)I + i] : 0.f;
+          }
+          const int r = i & 7;
+          *reinterpret_cast<uint4*>(bf + (i >> 3) * 1024 + r * 128 + ((c ^ r) << 4)) = pack_bf16x8(f);
+        }
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (!tail) ++done;
     committed = j + 1;
-    if (tid == 0) {
+    if (tid == kIssuer) {
       // stage s is consumed: refill it with step j + S
       if (j + S < nsteps && k + S < a.nk_full) { issue(j + S); issued = j + S + 1; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -206,46 +248,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
                    : "memory");
     }
   }
-  if (ok) {
+  if (ok && nsteps > 0) {
     const int jl = nsteps - 1;
     const bool fail = !mbar_wait(bar_mma + 8u * (jl & 1), (uint32_t)((jl >> 1) & 1));
     if (__syncthreads_or(fail)) ok = false;
   }
+  const bool has_d = ok && nsteps > 0;             // this CTA holds a valid partial D
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    for (int m = 0; m < nM; ++m) {
-      const int i = m * 128 + warp * 32 + lane;
-      for (int c0 = 0; c0 < a.N; c0 += 16) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15])
-            : "r"(tmem + lane_base + (uint32_t)(m * 256 + c0)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (i < I) {
-          float* g = a.G + (size_t)i * I;        // column i of G (= row i by symmetry)
-          if (a.vec4) {
-#pragma unroll
-            for (int u = 0; u < 16; u += 4) {
-              const int jj = c0 + u;
-              if (jj < I)
-                atomicAdd(reinterpret_cast<float4*>(g + jj),
-                          make_float4(__uint_as_float(r[u]), __uint_as_float(r[u + 1]),
-                                      __uint_as_float(r[u + 2]), __uint_as_float(r[u + 3])));
-            }
-          } else {
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-              if (c0 + u < I) atomicAdd(g + c0 + u, __uint_as_float(r[u]));
-          }
-        }
-      }
-    }
-  } else if (tid == 0) {
+  if (!ok && tid == kIssuer) {
     a.G[0] = __int_as_float(0x7fc00000);           // NaN: the solve reports a numeric failure
     // bounded waits for this CTA's copies and MMAs still in flight
     for (int j = done; j < issued; ++j) (void)mbar_wait(bar_full + 8u * (uint32_t)(j % S), (uint32_t)((j / S) & 1));
@@ -254,10 +264,123 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
       (void)mbar_wait(bar_mma + 8u * (jl & 1), (uint32_t)((jl >> 1) & 1));
     }
   }
+  // Epilogue, by column passes of at most 128 columns: every CTA of the
+  // cluster moves its partial D (rows < I) from tensor memory into its own
+  // shared memory (the stages are free now), the cluster synchronises, and
+  // CTA r sums rows [r I / cs, (r + 1) I / cs) over the cluster's CTAs through
+  // distributed shared memory and adds them into G.  Every CTA takes part in
+  // every cluster barrier, whatever its state, so a failed CTA cannot block
+  // its peers.
+  uint32_t crank, csize;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+  float* dsm = reinterpret_cast<float*>(sm + o_bf);
+  const uint32_t dsm_s = sb + o_bf;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int r0 = (int)(crank * (uint32_t)I / csize), r1 = (int)((crank + 1) * (uint32_t)I / csize);
+  // widest pass (a multiple of 16 columns) whose I x (W + 4) floats fit below the barriers
+  const int wp = min(a.N, (((int)(o_bar / (4u * (uint32_t)I)) - 4) / 16) * 16);
+  for (int h = 0; h * wp < a.N; ++h) {
+    const int W = min(wp, a.N - h * wp), ld = W + 4;
+    if (!has_d) {                                  // contribute zeros
+      for (int e = tid; e < I * (W >> 2); e += kThreads) {
+        const int i = e / (W >> 2), c = e - i * (W >> 2);
+        *reinterpret_cast<float4*>(dsm + (size_t)i * ld + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else if (warp < 4) {
+      for (int m = 0; m < nM; ++m) {
+        const int i = m * 128 + warp * 32 + lane;
+        for (int c0 = 0; c0 < W; c0 += 16) {
+          uint32_t r[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(tmem + lane_base + (uint32_t)(m * 256 + h * wp + c0)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (i < I) {
+            float4* d = reinterpret_cast<float4*>(dsm + (size_t)i * ld + c0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              d[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                                 __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
+          }
+        }
+      }
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    {
+      // two items per thread and iteration: 2 x cs remote loads in flight
+      const int w4 = W >> 2, n = (r1 - r0) * w4;
+      for (int e0 = tid; e0 < n; e0 += 2 * kThreads) {
+        float4 v[2][kCluster];
+        int ii[2], jj[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const int e = e0 + x * kThreads;
+          const int row = e / w4;
+          ii[x] = r0 + row;
+          const int jl = (e - row * w4) * 4;
+          jj[x] = (e < n) ? h * wp + jl : I;          // I marks an idle slot
+          const uint32_t off = dsm_s + (uint32_t)(((size_t)ii[x] * ld + jl) * 4);
+#pragma unroll
+          for (int q = 0; q < kCluster; ++q) {
+            v[x][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < (int)csize && jj[x] < I) {
+              uint32_t ra;
+              asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(off), "r"(q));
+              asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
+                           : "=f"(v[x][q].x), "=f"(v[x][q].y), "=f"(v[x][q].z), "=f"(v[x][q].w)
+                           : "r"(ra));
+            }
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const int i = ii[x], j = jj[x];
+          if (j >= I) continue;
+          float4 acc = v[x][0];
+#pragma unroll
+          for (int q = 1; q < kCluster; ++q) {
+            acc.x += v[x][q].x; acc.y += v[x][q].y; acc.z += v[x][q].z; acc.w += v[x][q].w;
+          }
+          float* g = a.G + (size_t)i * I + j;        // column i of G (= row i by symmetry)
+          if (a.vec4) {
+            atomicAdd(reinterpret_cast<float4*>(g), acc);
+          } else {
+            atomicAdd(g, acc.x);
+            if (j + 1 < I) atomicAdd(g + 1, acc.y);
+            if (j + 2 < I) atomicAdd(g + 2, acc.z);
+            if (j + 3 < I) atomicAdd(g + 3, acc.w);
+          }
+        }
+      }
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// Co-resident clusters of kCluster CTAs for a dynamic shared-memory size,
+// queried once per (device, size).
+int max_clusters(int dev, size_t smem, const cudaLaunchConfig_t& cfg) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({dev, smem});
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gram_tc, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  cache[{dev, smem}] = n;
+  return n;
 }
 
 size_t tc_smem_bytes(int I, int nM, int S) {
@@ -297,11 +420,32 @@ cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float*
   const size_t smem = tc_smem_bytes(a.I, a.nM, S);
   if (smem > (size_t)lim) return cudaErrorNotSupported;
   a.stages = S;
-  int grid = nsm > 0 ? nsm : 1;
-  if (grid > a.nk) grid = a.nk;
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_tc<<<grid, kThreads, smem, st>>>(a);
+  // clusters of kCluster CTAs when every CTA of every co-resident cluster gets
+  // at least one step; otherwise single-CTA clusters
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr; cfg.numAttrs = 1;
+  int cs = 1, grid = (nsm > 0 ? nsm : 1);
+  cfg.gridDim = dim3(kCluster * ((nsm + kCluster - 1) / kCluster));
+  const int ncl = a.nk >= 2 * kCluster ? max_clusters(dev, smem, cfg) : 0;
+  if (ncl > 0) {
+    cs = kCluster;
+    grid = ncl * kCluster;
+    while (grid > a.nk) grid -= kCluster;
+  } else {
+    if (grid > a.nk) grid = a.nk;
+  }
+  attr[0].val.clusterDim.x = cs;
+  cfg.gridDim = dim3(grid);
+  e = cudaLaunchKernelEx(&cfg, k_gram_tc, a);
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }

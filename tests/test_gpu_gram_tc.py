@@ -6,8 +6,9 @@ the same BF16-rounded entries (tolerance: FP32 accumulation, 2e-5 of max|G|),
 and with the FP64 Gram of the unrounded tensor (tolerance: BF16 input
 rounding, 1e-2 of max|G|).  Shapes cover one and two 128-row tiles, N not a
 multiple of 128, a ragged last 64-column step, a tensor shorter than one
-step, I = 1 and the largest supported I = 256, and scalar (I % 4 != 0) and
-vector atomics.  The compressed solve with BF16 compression and FP32
+step, I = 1 and the largest supported I = 256, scalar (I % 4 != 0) and
+vector atomics, and both single-CTA and 8-CTA-cluster reductions (16 or more
+64-column steps).  The compressed solve with BF16 compression and FP32
 refinement in the original space is held to the oracle's FP64 fit.
 """
 import numpy as np
@@ -39,7 +40,7 @@ def bf16_round(x):
 
 
 @pytest.mark.parametrize("dims", [(200, 200, 200), (128, 33, 7), (130, 5, 13), (1, 64, 2), (7, 3, 3),
-                                  (256, 64, 3), (97, 11, 12)])
+                                  (256, 64, 3), (97, 11, 12), (100, 40, 30), (131, 30, 40), (256, 50, 70)])
 def test_gram_bf16_matches_definition(cpd, dims):
     g = np.random.default_rng(sum(dims) + 1)
     T = g.standard_normal(dims).astype(np.float32)
