@@ -109,6 +109,40 @@ def workload():
     return c["T"], c["R"]
 
 
+# sources whose kernels a stage times; a DRAM-traffic figure recorded in
+# profiles/traffic.json is reported only while these files are unchanged
+STAGE_SOURCES = {
+    "dgn_core": ["k_dgn.cu", "dgn_cta.cuh", "solver.cuh", "common.cuh", "kernels.h"],
+    "gram_bf16_tc": ["k_gram_tc.cu", "kernels.h"],
+}
+
+
+def sources_sha256(stage: str):
+    import hashlib
+    files = STAGE_SOURCES.get(stage)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2110_05997_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(stage: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu
+    capture recorded in profiles/traffic.json, or None when there is none or
+    the kernel's sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        rec = json.load(fh).get(stage)
+    if not rec or rec.get("sources_sha256") != sources_sha256(stage):
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: dict, clk_mhz):
     """Roofline entry of a stage: algorithmic bytes or flops per launch over
     its measured average launch time."""
@@ -295,8 +329,20 @@ def run_ours(args, rank, world, local_rank):
     if dom[0] is not None:
         per = dom[1]["ms"] / dom[1]["launches"]
         roof = algorithmic(dom[0], dims, R, infos[-1], per, pk, csum["sm_mhz"])
-        roof.update(kernel=dom[0], launches=dom[1]["launches"], ms_per_launch=per, traffic=None,
+        roof.update(kernel=dom[0], launches=dom[1]["launches"], ms_per_launch=per, traffic=measured_traffic(dom[0]),
                     peak_source=pk["src"], region="separate profiled K-step region, direct launches")
+    # the same roofline entry for the other stages that have a bound
+    stage_roofs = {}
+    for k, v in prof.items():
+        if k == dom[0] or k not in ("gram_bf16_tc", "gram_fp32", "refine_pass"):
+            continue
+        n = v["launches"]
+        if k == "refine_pass":
+            # passes after the stop test exit at once: time the working ones
+            n = min(n, args.steps * (int(infos[-1].get("refine_iters", 0)) + 1))
+        r = algorithmic(k, dims, R, infos[-1], v["ms"] / max(n, 1), pk, csum["sm_mhz"])
+        r.update(traffic=measured_traffic(k), working_launches=n)
+        stage_roofs[k] = r
     stages = {k: dict(ms_per_step=v["ms"] / args.steps, launches_per_step=v["launches"] / args.steps)
               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -306,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
                             rank=R, gram_precision=args.gram, refine_maxiter=REFINE_MAXITER,
                             global_batch=world, parallelism=f"independent CPD per GPU x{world}",
                             l2="flushed between steps (256 MB write)", launch="cached CUDA graph per solve"),
-                e2e=e2e, gpu_launches=int(launches), roofline=roof, stages=stages,
+                e2e=e2e, gpu_launches=int(launches), roofline=roof, stage_rooflines=stage_roofs, stages=stages,
                 profiled_ms_per_step=ms_prof / args.steps,
                 clocks=csum, solve=dict(core_iters=info["iters"], core_stop=info["stop_name"],
                                         core_cg=info["cg_total"], core_dims=info["core_dims"][:3],
