@@ -67,7 +67,10 @@ typedef enum {
 typedef enum {
   CPD_INIT_MLSVD = 0,   /* R core entries of largest |s| as rank-one terms          */
   CPD_INIT_RANDOM = 1,  /* N(0,1) by Box-Muller on SplitMix64 stream 2 of `seed`    */
-  CPD_INIT_GIVEN = 2    /* caller's W0 in the ORIGINAL space (projected under compression) */
+  CPD_INIT_GIVEN = 2,   /* caller's W0 in the ORIGINAL space (projected under compression) */
+  CPD_INIT_LEARNED = 3  /* the learned initialiser's factors for the core, or the MLSVD
+                           start when that has the smaller residual (batched solver
+                           only: cpd_batch_solve_learned; no counterpart in the thesis) */
 } cpd_init;
 
 /* Arithmetic of the compression Gram matrices. */
@@ -110,6 +113,7 @@ typedef struct {
   int refine_iters;     /* refinement iterations run                             */
   int refine_stop_reason;
   int refine_cg_total;
+  int init_used;        /* 1 when dGN started from the learned initialiser's factors */
   double refine_rel_err;  /* ||T - T_k|| / ||T|| after refinement (FP64-accumulated) */
 } cpd_info;
 
@@ -206,8 +210,95 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
                     const int64_t* w_off, float* lam_packed, const int64_t* l_off,
                     cpd_info* infos, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- learned initialiser ---------------------------------------------------
+ * No counterpart in the thesis, which starts dGN from random factors or from
+ * the compressed core (Sec. 4.1.2): a multilayer perceptron proposes the
+ * initial factors for dGN on a compressed core, and the solver keeps the
+ * MLSVD start whenever that has the smaller residual.
+ *
+ *   input row x (CPD_INITNET_IN_PAD floats): S / ||S|| with S the core
+ *     (I1 x I2 x I3 <= 16^3) zero-padded into a 16 x 16 x 16 column-major
+ *     block (entries 0..4095), then the rank one-hot (entry 4096 + R - 1,
+ *     R <= 8), then zeros;
+ *   hidden layers: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2) (512 each);
+ *   output row y (CPD_INITNET_OUT floats): y[l*128 + r*16 + i] is entry
+ *     (i, r) of the mode-l factor divided by ||S||^(1/3) (i < 16, r < 8).
+ *   parameters, one FP32 vector of cpd_initnet_param_count() floats:
+ *     W1 (512 x 4160, row-major) | b1 (512) | W2 (512 x 512) | b2 | W3 (384 x 512) | b3 (384).
+ * Products run on BF16 tensor cores (operands rounded to BF16, FP32
+ * accumulation).  Matrices are row-major, one sample per row.
+ */
+#define CPD_INITNET_CORE 16
+#define CPD_INITNET_RANK 8
+#define CPD_INITNET_IN 4104
+#define CPD_INITNET_IN_PAD 4160
+#define CPD_INITNET_HIDDEN 512
+#define CPD_INITNET_OUT 384
+
+size_t cpd_initnet_param_count(void);
+/* Workspace bytes of cpd_initnet_forward / cpd_initnet_grad for B samples. */
+size_t cpd_initnet_workspace_size(int B);
+/* Y (B x 384, device) = network(X) for X (B x 4160, device, padding zero). */
+int cpd_initnet_forward(const float* params, const float* X, int B, float* Y, void* workspace,
+                        size_t ws_bytes, void* stream);
+/*
+ * Gradient of a training loss with respect to all parameters, into grad
+ * (param_count floats, device; overwritten), and the loss into *loss_dev
+ * (device double).  With a target (B x 384, device): the masked mean
+ * squared error  loss = sum_{b,o} mask[b,o] (y[b,o] - target[b,o])^2 / sum mask.
+ * With target == NULL: the reconstruction error of the input cores by the
+ * proposed factors (the CP objective on each core, Sec. 3.1),
+ *   loss = (1/B) sum_b ||S_b / ||S_b|| - sum_r a_r (x) b_r (x) c_r||^2,
+ * factors taken from y_b where mask[b] is 1 (the entries that exist).
+ */
+int cpd_initnet_grad(const float* params, const float* X, const float* target, const float* mask,
+                     int B, float* grad, double* loss_dev, void* workspace, size_t ws_bytes,
+                     void* stream);
+/* One Adam step (Kingma & Ba) on params with moments m, v (device), step >= 1. */
+int cpd_initnet_adam(float* params, float* m, float* v, const float* grad, int step, double lr,
+                     double beta1, double beta2, double eps, void* stream);
+
+/*
+ * Batched solves that feed and use the learned initialiser (same items,
+ * limits and outputs as cpd_batch_solve; compression is always on; items
+ * with R > 8 or a core mode above 16 always start from the MLSVD start).
+ *  cpd_batch_initnet_data: the plain method (MLSVD start) on every item, plus
+ *    per item b the network input row X[b] (4160 floats) and the solver's
+ *    core CPD as a training target[b] (384 floats, the output layout above;
+ *    terms by decreasing weight, signs as in the outputs, each column scaled
+ *    to (lambda_r / ||S||)^(1/3); a zero row when the core solve did not
+ *    reach rel_err < 1e-3 or a term's weight exceeds 8 ||S||: no target from
+ *    a stalled or degenerate CPD) and mask[b] (1 on the factor entries that
+ *    exist: rows below the core dims, columns below R; all 0 for ineligible items).
+ *    X, target, mask: device, row-major; any of them may be NULL.
+ *  cpd_batch_solve_learned: the network (params) proposes each eligible
+ *    item's start; cpd_info.init_used tells which start dGN took.
+ */
+size_t cpd_batch_ex_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts);
+int cpd_batch_initnet_data(int B, const float* T_packed, const int64_t* t_off, const int* dims,
+                           const int* ranks, const cpd_options* opts, float* W_packed,
+                           const int64_t* w_off, float* lam_packed, const int64_t* l_off,
+                           float* X, float* target, float* mask, cpd_info* infos,
+                           void* workspace, size_t ws_bytes, void* stream);
+int cpd_batch_solve_learned(int B, const float* T_packed, const int64_t* t_off, const int* dims,
+                            const int* ranks, const cpd_options* opts, const float* params,
+                            float* W_packed, const int64_t* w_off, float* lam_packed,
+                            const int64_t* l_off, cpd_info* infos, void* workspace,
+                            size_t ws_bytes, void* stream);
+
 /* ---- component calls (the same device code the solvers run), for testing
  *      and for callers that compose the steps themselves ---------------------- */
+
+/*
+ * cpd_gemm_bf16 — the tensor-core GEMM the learned initialiser runs on:
+ *   D[m*ldd + n] (=, or += when accumulate) epi(sum_k A[m*sam + k*sak] B[n*sbn + k*sbk])
+ * for m < M, n < N, k < K; epi adds bias[n] (if non-NULL), applies ReLU (if
+ * relu), and zeroes entries where mask[m*ldm + n] <= 0 (if mask non-NULL).
+ * A, B, D, bias, mask: device FP32; operands rounded to BF16, FP32 accumulation.
+ */
+int cpd_gemm_bf16(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B,
+                  int64_t sbn, int64_t sbk, float* D, int64_t ldd, const float* bias, int relu,
+                  const float* mask, int64_t ldm, int accumulate, void* stream);
 
 /*
  * cpd_core_eval — residual and gradient on a small tensor by one CTA

@@ -24,14 +24,18 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too 
           -6: "unsupported configuration"}
 STOP = {0: "none", 1: "rel_err", 2: "step", 3: "improvement", 4: "grad", 5: "avg_err",
         6: "avg_improvement", 7: "divergence", 8: "maxiter"}
-INIT = {"mlsvd": 0, "random": 1, "given": 2}
+INIT = {"mlsvd": 0, "random": 1, "given": 2, "learned": 3}
+INITNET_CORE, INITNET_RANK, INITNET_IN, INITNET_IN_PAD, INITNET_HIDDEN, INITNET_OUT = 16, 8, 4104, 4160, 512, 384
 GRAM = {"fp32": 0, "bf16": 1}
 F32, F64 = 0, 1
 
 EXPORTS = ["cpd_default_options", "cpd_status_string", "cpd_workspace_size", "cpd_compress",
            "cpd_dgn_solve", "cpd_batch_workspace_size", "cpd_batch_solve", "cpd_core_eval",
            "cpd_jtj_apply", "cpd_mode_gram", "cpd_refine_eval", "cpd_launch_count",
-           "cpd_profile_enable", "cpd_profile_read", "cpd_dgn_solve_noalloc"]
+           "cpd_profile_enable", "cpd_profile_read", "cpd_dgn_solve_noalloc",
+           "cpd_initnet_param_count", "cpd_initnet_workspace_size", "cpd_initnet_forward",
+           "cpd_initnet_grad", "cpd_initnet_adam", "cpd_batch_ex_workspace_size",
+           "cpd_batch_initnet_data", "cpd_batch_solve_learned", "cpd_gemm_bf16"]
 
 
 class CpdError(RuntimeError):
@@ -53,7 +57,7 @@ class cpd_info(C.Structure):
                 ("cg_total", C.c_int), ("rel_err", C.c_double), ("mu", C.c_double),
                 ("grad_inf", C.c_double), ("core_dims", C.c_int * MAX_ORDER),
                 ("refine_iters", C.c_int), ("refine_stop_reason", C.c_int),
-                ("refine_cg_total", C.c_int), ("refine_rel_err", C.c_double)]
+                ("refine_cg_total", C.c_int), ("init_used", C.c_int), ("refine_rel_err", C.c_double)]
 
     def as_dict(self):
         return dict(status=self.status, iters=self.iters, stop=self.stop_reason,
@@ -61,7 +65,7 @@ class cpd_info(C.Structure):
                     rel_err=self.rel_err, mu=self.mu, grad_inf=self.grad_inf,
                     core_dims=list(self.core_dims), refine_iters=self.refine_iters,
                     refine_stop=self.refine_stop_reason, refine_cg_total=self.refine_cg_total,
-                    refine_rel_err=self.refine_rel_err)
+                    refine_rel_err=self.refine_rel_err, init_used=self.init_used)
 
 
 _lib = None
@@ -103,6 +107,28 @@ def lib():
         L.cpd_refine_eval.restype = C.c_int
         L.cpd_dgn_solve_noalloc.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, optp, vp, fp, fp, infop, vp]
         L.cpd_dgn_solve_noalloc.restype = C.c_int
+        L.cpd_initnet_param_count.argtypes = []
+        L.cpd_initnet_param_count.restype = C.c_size_t
+        L.cpd_initnet_workspace_size.argtypes = [C.c_int]
+        L.cpd_initnet_workspace_size.restype = C.c_size_t
+        L.cpd_initnet_forward.argtypes = [vp, vp, C.c_int, fp, vp, C.c_size_t, vp]
+        L.cpd_initnet_forward.restype = C.c_int
+        L.cpd_initnet_grad.argtypes = [vp, vp, vp, vp, C.c_int, fp, dp, vp, C.c_size_t, vp]
+        L.cpd_initnet_grad.restype = C.c_int
+        L.cpd_initnet_adam.argtypes = [fp, fp, fp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, vp]
+        L.cpd_initnet_adam.restype = C.c_int
+        L.cpd_batch_ex_workspace_size.argtypes = [C.c_int, ip, ip, optp]
+        L.cpd_batch_ex_workspace_size.restype = C.c_size_t
+        L.cpd_batch_initnet_data.argtypes = [C.c_int, vp, i64p, ip, ip, optp, fp, i64p, fp, i64p, fp, fp,
+                                             fp, infop, vp, C.c_size_t, vp]
+        L.cpd_batch_initnet_data.restype = C.c_int
+        L.cpd_batch_solve_learned.argtypes = [C.c_int, vp, i64p, ip, ip, optp, vp, fp, i64p, fp, i64p,
+                                              infop, vp, C.c_size_t, vp]
+        L.cpd_batch_solve_learned.restype = C.c_int
+        L.cpd_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int64, C.c_int64, vp, C.c_int64,
+                                    C.c_int64, fp, C.c_int64, vp, C.c_int, vp, C.c_int64, C.c_int, vp]
+        L.cpd_gemm_bf16.restype = C.c_int
         L.cpd_launch_count.argtypes = []
         L.cpd_launch_count.restype = C.c_longlong
         L.cpd_profile_enable.argtypes = [C.c_int]
@@ -330,6 +356,109 @@ def cpd_batch_solve(T_packed, t_off, dims, ranks, opts: cpd_options | None = Non
                                lof, infos, _ptr(workspace), workspace.numel(), _stream(stream))
     _check("cpd_batch_solve", st)
     return W, lam, w_off, l_off, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def _batch_marshal(T_packed, t_off, dims, ranks):
+    import torch
+    B = len(ranks)
+    dev = T_packed.device
+    w_off, l_off, wo, lo = [], [], 0, 0
+    for b in range(B):
+        w_off.append(wo)
+        l_off.append(lo)
+        wo += int(ranks[b]) * sum(int(x) for x in dims[b])
+        lo += int(ranks[b])
+    W = torch.empty(max(wo, 1), dtype=torch.float32, device=dev)
+    lam = torch.empty(max(lo, 1), dtype=torch.float32, device=dev)
+    d = (C.c_int * (3 * B))(*[int(x) for row in dims for x in row])
+    r = (C.c_int * B)(*[int(x) for x in ranks])
+    to = (C.c_int64 * B)(*[int(x) for x in t_off])
+    return B, dev, W, lam, w_off, l_off, d, r, to, (C.c_int64 * B)(*w_off), (C.c_int64 * B)(*l_off)
+
+
+def cpd_batch_initnet_data(T_packed, t_off, dims, ranks, opts: cpd_options | None = None, stream=None,
+                           workspace=None):
+    """The plain method (MLSVD start) on every item, plus the network input rows
+    X (B x 4160), the core CPDs as training targets (B x 384) and their masks."""
+    import torch
+    opts = opts or cpd_default_options()
+    B, dev, W, lam, w_off, l_off, d, r, to, wof, lof = _batch_marshal(T_packed, t_off, dims, ranks)
+    X = torch.empty(B, INITNET_IN_PAD, dtype=torch.float32, device=dev)
+    tgt = torch.empty(B, INITNET_OUT, dtype=torch.float32, device=dev)
+    msk = torch.empty(B, INITNET_OUT, dtype=torch.float32, device=dev)
+    infos = (cpd_info * B)()
+    if workspace is None:
+        workspace = _workspace(int(lib().cpd_batch_ex_workspace_size(B, d, r, C.byref(opts))), dev)
+    st = lib().cpd_batch_initnet_data(B, _ptr(T_packed), to, d, r, C.byref(opts), _ptr(W), wof, _ptr(lam), lof,
+                                      _ptr(X), _ptr(tgt), _ptr(msk), infos, _ptr(workspace), workspace.numel(),
+                                      _stream(stream))
+    _check("cpd_batch_initnet_data", st)
+    return X, tgt, msk, W, lam, w_off, l_off, [i.as_dict() for i in infos]
+
+
+def cpd_batch_solve_learned(T_packed, t_off, dims, ranks, params, opts: cpd_options | None = None,
+                            stream=None, workspace=None, want_infos: bool = True):
+    """Batched solves whose dGN starts from the learned initialiser's factors
+    (or the MLSVD start when that has the smaller residual)."""
+    opts = opts or cpd_default_options()
+    B, dev, W, lam, w_off, l_off, d, r, to, wof, lof = _batch_marshal(T_packed, t_off, dims, ranks)
+    infos = (cpd_info * B)() if want_infos else None
+    if workspace is None:
+        workspace = _workspace(int(lib().cpd_batch_ex_workspace_size(B, d, r, C.byref(opts))), dev)
+    st = lib().cpd_batch_solve_learned(B, _ptr(T_packed), to, d, r, C.byref(opts), _ptr(params), _ptr(W), wof,
+                                       _ptr(lam), lof, infos, _ptr(workspace), workspace.numel(),
+                                       _stream(stream))
+    _check("cpd_batch_solve_learned", st)
+    return W, lam, w_off, l_off, ([i.as_dict() for i in infos] if infos is not None else None)
+
+
+def cpd_initnet_param_count() -> int:
+    return int(lib().cpd_initnet_param_count())
+
+
+def cpd_initnet_workspace_size(B: int) -> int:
+    return int(lib().cpd_initnet_workspace_size(int(B)))
+
+
+def cpd_initnet_forward(params, X, stream=None, workspace=None):
+    import torch
+    B = X.shape[0]
+    Y = torch.empty(B, INITNET_OUT, dtype=torch.float32, device=X.device)
+    if workspace is None:
+        workspace = _workspace(cpd_initnet_workspace_size(B), X.device)
+    _check("cpd_initnet_forward", lib().cpd_initnet_forward(_ptr(params), _ptr(X), B, _ptr(Y), _ptr(workspace),
+                                                            workspace.numel(), _stream(stream)))
+    return Y
+
+
+def cpd_initnet_grad(params, X, target, mask, grad=None, loss=None, stream=None, workspace=None):
+    """Gradient of the masked mean squared error (into ``grad``) and the loss (device double)."""
+    import torch
+    B = X.shape[0]
+    if grad is None:
+        grad = torch.empty_like(params)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=X.device)
+    if workspace is None:
+        workspace = _workspace(cpd_initnet_workspace_size(B), X.device)
+    _check("cpd_initnet_grad", lib().cpd_initnet_grad(_ptr(params), _ptr(X), _ptr(target), _ptr(mask), B, _ptr(grad),
+                                                      _ptr(loss), _ptr(workspace), workspace.numel(),
+                                                      _stream(stream)))
+    return grad, loss
+
+
+def cpd_initnet_adam(params, m, v, grad, step: int, lr: float = 1e-3, beta1: float = 0.9,
+                     beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    _check("cpd_initnet_adam", lib().cpd_initnet_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step),
+                                                      float(lr), float(beta1), float(beta2), float(eps),
+                                                      _stream(stream)))
+
+
+def cpd_gemm_bf16(M, N, K, A, sam, sak, B, sbn, sbk, D, ldd, bias=None, relu=False, mask=None, ldm=0,
+                  accumulate=False, stream=None) -> None:
+    _check("cpd_gemm_bf16", lib().cpd_gemm_bf16(int(M), int(N), int(K), _ptr(A), int(sam), int(sak), _ptr(B),
+                                                int(sbn), int(sbk), _ptr(D), int(ldd), _ptr(bias), int(bool(relu)),
+                                                _ptr(mask), int(ldm), int(bool(accumulate)), _stream(stream)))
 
 
 def cpd_launch_count() -> int:

@@ -136,10 +136,33 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
   double normS, meanabs;
   load_tensor(s, a.S, a.s_f64, Sbuf, b.red, normS, meanabs);
   fill_cg_table(a.cgtab, a.cgtab_len, a.seed, a.cg_a, a.cg_b);
-  init_factors<L>(s, b, a.init, a.W0, a.seed, chosen);
-  balance<L>(s, b);
   double fsq, ginf;
-  core_pass<L>(s, b, fsq, ginf);
+  __shared__ int s_init_used;
+  if (a.init == CPD_INIT_LEARNED) {
+    // two candidate starts: the MLSVD-energy start and the network's factors
+    // (a.W0); dGN starts from the one with the smaller residual (the MLSVD
+    // start is the fallback).  a.W_out holds the first candidate meanwhile.
+    init_factors<L>(s, b, CPD_INIT_MLSVD, nullptr, a.seed, chosen);
+    balance<L>(s, b);
+    double f_mlsvd, g_mlsvd;
+    core_pass<L>(s, b, f_mlsvd, g_mlsvd);
+    for (int j = threadIdx.x; j < s.n; j += blockDim.x) a.W_out[j] = b.W[j];
+    init_factors<L>(s, b, CPD_INIT_GIVEN, a.W0, a.seed, chosen);
+    balance<L>(s, b);
+    core_pass<L>(s, b, fsq, ginf);
+    if (threadIdx.x == 0) s_init_used = (isfinite(fsq) && !(fsq > f_mlsvd)) ? 1 : 0;
+    __syncthreads();
+    if (!s_init_used) {
+      for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = a.W_out[j];
+      __syncthreads();
+      core_pass<L>(s, b, fsq, ginf);
+    }
+  } else {
+    init_factors<L>(s, b, a.init, a.W0, a.seed, chosen);
+    balance<L>(s, b);
+    core_pass<L>(s, b, fsq, ginf);
+    if (threadIdx.x == 0) s_init_used = 0;
+  }
   if (threadIdx.x == 0) {
     st.mu = a.mu0 >= 0.0 ? a.mu0 : a.tau * meanabs;
     st.F = 0.5 * fsq;
@@ -189,6 +212,7 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
     DevResult* r = a.res;
     r->status = st.status; r->iters = st.iters; r->stop = st.stop; r->cg_total = st.cg_total;
     r->kglob = st.kglob; r->rel_err = st.rel_err; r->mu = st.mu; r->grad_inf = st.grad_inf;
+    r->pad0 = s_init_used;                     // 1: started from the learned factors
     r->normS = st.normS;
   }
 }

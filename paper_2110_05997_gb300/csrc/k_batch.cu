@@ -116,6 +116,21 @@ __host__ __device__ inline BatchLayout batch_layout(int dmax, int Rmax, int maxi
 
 __host__ __device__ inline int g_floats(int dmax) { return (dmax * dmax + 3) & ~3; }   // 16-byte multiple
 
+// Per-item store between the phases of a phased run (offsets in floats):
+// core (P^3) | U blocks (3 x dmax x P, block l at dmax * P * l) | meta
+// (core dims as ints, ||S||, eligibility for the learned start).
+struct StoreLayout { size_t core, U, meta, total; };
+__host__ __device__ inline StoreLayout store_layout(int dmax, int Rmax) {
+  const size_t P = (size_t)(Rmax < dmax ? Rmax : dmax);
+  auto up = [](size_t x) { return (x + 63) & ~(size_t)63; };
+  StoreLayout l{};
+  l.core = 0;
+  l.U = up(P * P * P);
+  l.meta = l.U + up(3 * (size_t)dmax * P);
+  l.total = l.meta + 64;
+  return l;
+}
+
 __host__ __device__ inline size_t batch_compress_smem(int dmax, int Rmax) {
   const int P = Rmax < dmax ? Rmax : dmax;
   return (size_t)g_floats(dmax) * 4 + (size_t)kGTile * kGLd * 4 + (size_t)dmax * P * 4 + 256 +
@@ -152,7 +167,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
     int core[3] = {d[0], d[1], d[2]};
     const float* S = T;
     float* U = gs + lay.U;
-    if (a.compress) {
+    const StoreLayout sl = store_layout(dmax, Rmax);
+    float* slot = a.store ? a.store + (size_t)it.b * a.store_floats : nullptr;
+    int* meta_i = slot ? reinterpret_cast<int*>(slot + sl.meta) : nullptr;
+    if (a.phase == 2) {
+      // the core and bases stored by phase 1; U blocks sit at dmax * P0 * l
+      core[0] = meta_i[0]; core[1] = meta_i[1]; core[2] = meta_i[2];
+      S = slot + sl.core;
+      U = slot + sl.U;
+    } else if (a.compress) {
       // ST-MLSVD: mode by mode on the partially projected tensor
       const float* cur = T;
       float* outs[3] = {gs + lay.Y1, gs + lay.Y2, gs + lay.S};
@@ -181,6 +204,59 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
       }
       S = gs + lay.S;
     }
+    if (a.phase == 1) {
+      // store the core, the bases and the network's input row; no solve
+      const int nc = core[0] * core[1] * core[2];
+      float* dst = slot + sl.core;
+      double sq = 0.0;
+      for (int e = threadIdx.x; e < nc; e += blockDim.x) {
+        const float v = S[e];
+        dst[e] = v;
+        sq += (double)v * (double)v;
+      }
+      {
+        int offU = 0;
+        for (int l = 0; l < 3; ++l) {
+          const int P = R < d[l] ? R : d[l];
+          for (int e = threadIdx.x; e < d[l] * P; e += blockDim.x) slot[sl.U + (size_t)dmax * P0 * l + e] = U[offU + e];
+          offU += d[l] * P;
+        }
+      }
+      __shared__ double s_sq;
+      {
+        float sqf[1] = {(float)sq};
+        double o[1];
+        block_sum<1>(sqf, o, reinterpret_cast<double*>(smem_raw));
+        if (threadIdx.x == 0) s_sq = o[0];
+      }
+      __syncthreads();
+      const float nrm = (float)sqrt(s_sq);
+      const bool elig = R <= CPD_INITNET_RANK && core[0] <= CPD_INITNET_CORE && core[1] <= CPD_INITNET_CORE &&
+                        core[2] <= CPD_INITNET_CORE && nrm > 0.f;
+      if (threadIdx.x == 0) {
+        meta_i[0] = core[0]; meta_i[1] = core[1]; meta_i[2] = core[2];
+        slot[sl.meta + 3] = nrm;
+        meta_i[4] = elig ? 1 : 0;
+      }
+      if (a.X) {
+        float* x = a.X + (size_t)it.b * CPD_INITNET_IN_PAD;
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        for (int e = threadIdx.x; e < CPD_INITNET_IN_PAD; e += blockDim.x) {
+          float v = 0.f;
+          if (elig) {
+            if (e < 4096) {
+              const int i = e & 15, j = (e >> 4) & 15, k = e >> 8;
+              if (i < core[0] && j < core[1] && k < core[2]) v = S[i + core[0] * (j + core[1] * k)] * inv;
+            } else if (e == 4096 + R - 1) {
+              v = 1.f;
+            }
+          }
+          x[e] = v;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     // damped Gauss-Newton on the core (the single-CTA solver); an item whose
     // tensor would not fit the launched shared memory is refused, not run
     {
@@ -201,6 +277,26 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
     da.dims[0] = core[0]; da.dims[1] = core[1]; da.dims[2] = core[2]; da.dims[3] = 1;
     da.dev_dims = nullptr;
     da.S = S; da.s_f64 = 0; da.W0 = nullptr; da.init = a.init; da.seed = seed;
+    if (a.phase == 2 && a.init == CPD_INIT_LEARNED) {
+      // the network's proposal, scaled back by ||S||^(1/3), as stacked core-space
+      // blocks; the MLSVD start when the item is not eligible
+      if (meta_i[4] && a.Y) {
+        float* W0 = gs + lay.Wf;
+        const float* y = a.Y + (size_t)it.b * CPD_INITNET_OUT;
+        const float sc = cbrtf(slot[sl.meta + 3]);
+        int offC = 0;
+        for (int l = 0; l < 3; ++l) {
+          for (int q = threadIdx.x; q < core[l] * R; q += blockDim.x) {
+            const int r = q / core[l], i = q - r * core[l];
+            W0[offC + q] = y[l * 128 + r * 16 + i] * sc;
+          }
+          offC += core[l] * R;
+        }
+        da.W0 = W0;
+      } else {
+        da.init = CPD_INIT_MLSVD;
+      }
+    }
     da.tol = a.tol; da.tau = a.tau; da.cg_a = a.cg_a; da.cg_b = a.cg_b; da.maxiter = a.maxiter;
     da.mu0 = -1.0; da.k0 = 0; da.big_in_smem = 1; da.gscratch = nullptr;
     da.hist = hist; da.trace = nullptr; da.trace_cap = 0; da.trace_slot0 = 0;
@@ -226,12 +322,75 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
           }
           Wf[offF + q] = acc;
         }
-        offU += I * P;
+        offU += (a.phase == 2) ? dmax * P0 : I * P;
         offC += rk * R;
         offF += I * R;
       }
     }
     __syncthreads();
+    if (a.phase == 2 && a.target) {
+      // the core CPD as a training target: terms by decreasing weight, the
+      // outputs' sign rule, column (l, r) scaled to (lambda_r / ||S||)^(1/3)
+      float* tn = reinterpret_cast<float*>(smem_raw);              // 3 * R norms
+      float* ts = tn + 3 * kBatchMaxRank;                           // 3 * R signs
+      double* tl = reinterpret_cast<double*>(ts + 3 * kBatchMaxRank);
+      int* tp = reinterpret_cast<int*>(tl + kBatchMaxRank);
+      int offc[3] = {0, core[0] * R, (core[0] + core[1]) * R};
+      for (int q = threadIdx.x; q < 3 * R; q += blockDim.x) {
+        const int l = q / R, r = q - l * R, I = core[l];
+        const float* w = Wc + offc[l] + r * I;
+        double s2 = 0.0; float best = -1.f; int bi = 0;
+        for (int i = 0; i < I; ++i) {
+          s2 += (double)w[i] * (double)w[i];
+          if (fabsf(w[i]) > best) { best = fabsf(w[i]); bi = i; }
+        }
+        tn[q] = (float)sqrt(s2);
+        ts[q] = w[bi] < 0.f ? -1.f : 1.f;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        tl[r] = (double)tn[r] * (double)tn[R + r] * (double)tn[2 * R + r];
+        ts[2 * R + r] = ts[r] * ts[R + r];
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        int p = 0;
+        for (int t = 0; t < R; ++t) p += (tl[t] > tl[r] || (tl[t] == tl[r] && t < r)) ? 1 : 0;
+        tp[r] = p;
+      }
+      __syncthreads();
+      // only converged, non-degenerate core CPDs make targets: the solve
+      // reached rel_err < 1e-3 and no term outweighs the core 8 times
+      // (diverging, cancelling terms appear near swamps)
+      const float snrm = slot[sl.meta + 3];
+      __shared__ int s_tgt_ok;
+      if (threadIdx.x == 0) {
+        bool okc = meta_i[4] != 0 && dres->status == CPD_OK && dres->rel_err < 1e-3;
+        for (int r = 0; r < R; ++r) okc = okc && tl[r] <= 8.0 * (double)snrm;
+        s_tgt_ok = okc ? 1 : 0;
+      }
+      __syncthreads();
+      const bool elig = meta_i[4] != 0;             // the mask marks the entries that exist
+      const bool tgt_ok = s_tgt_ok != 0;
+      float* tg = a.target + (size_t)it.b * CPD_INITNET_OUT;
+      float* tm = a.tmask ? a.tmask + (size_t)it.b * CPD_INITNET_OUT : nullptr;
+      for (int e = threadIdx.x; e < CPD_INITNET_OUT; e += blockDim.x) { tg[e] = 0.f; if (tm) tm[e] = 0.f; }
+      __syncthreads();
+      if (elig) {
+        for (int l = 0; l < 3; ++l) {
+          const int I = core[l];
+          for (int q = threadIdx.x; q < I * R; q += blockDim.x) {
+            const int r = q / I, i = q - r * I;
+            const float nr = tn[l * R + r];
+            const float colscale = (float)cbrt(snrm > 0.f ? tl[r] / (double)snrm : 0.0);
+            const float v = nr > 0.f ? Wc[offc[l] + q] / nr * ts[l * R + r] * colscale : 0.f;
+            tg[l * 128 + tp[r] * 16 + i] = tgt_ok ? v : 0.f;
+            if (tm) tm[l * 128 + tp[r] * 16 + i] = 1.f;
+          }
+        }
+      }
+      __syncthreads();
+    }
     // output normalisation (unit columns, lambda, signs, descending lambda)
     float* nrm = reinterpret_cast<float*>(smem_raw);          // 3 * R
     float* sgn = nrm + 3 * kBatchMaxRank;                      // 3 * R
@@ -281,6 +440,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
       inf.cg_total = dres->cg_total; inf.rel_err = dres->rel_err; inf.mu = dres->mu;
       inf.grad_inf = dres->grad_inf;
       inf.core_dims[0] = core[0]; inf.core_dims[1] = core[1]; inf.core_dims[2] = core[2];
+      inf.init_used = dres->pad0;
       a.infos[it.b] = inf;
     }
     __syncthreads();
@@ -290,6 +450,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
 // Shared memory of one batch CTA: the larger of the compression phase and
 // the dGN phase; the dGN holds the core (P^3, P = min(Rmax, dmax)) or, without
 // compression, the whole item tensor (dmax^3).
+size_t batch_store_floats(int dmax, int Rmax) { return store_layout(dmax, Rmax).total; }
+
 size_t batch_smem_bytes(int dmax, int Rmax, int compress) {
   const int P = compress ? (Rmax < dmax ? Rmax : dmax) : dmax;
   int cd[CPD_MAX_ORDER] = {P, P, P, 1};
@@ -373,6 +535,116 @@ BatchPlan batch_plan(int B, int dmax, int Rmax, const cpd_options& o, size_t sme
 }
 }  // namespace
 
+namespace {
+
+// Workspace of a phased run: the plain plan, then the per-item store, the
+// network's inputs and outputs and its activation scratch.
+struct ExLayout { BatchPlan p; size_t store, X, Y, act, total; size_t store_floats; };
+ExLayout batch_ex_layout(int B, int dmax, int Rmax, const cpd_options& o, size_t smem) {
+  ExLayout e{};
+  e.p = batch_plan(B, dmax, Rmax, o, smem);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  e.store_floats = store_layout(dmax, Rmax).total;
+  size_t off = e.p.total;
+  e.store = off; off += up(sizeof(float) * e.store_floats * (size_t)B);
+  e.X = off; off += up(sizeof(float) * (size_t)CPD_INITNET_IN_PAD * B);
+  e.Y = off; off += up(sizeof(float) * (size_t)CPD_INITNET_OUT * B);
+  e.act = off; off += up(initnet_act_bytes(B));
+  e.total = off;
+  return e;
+}
+
+int launch_k_batch(const BatchArgs& a, int dmax, int Rmax, size_t smem, int ctas, cudaStream_t st) {
+  if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return CPD_ERR_CUDA;
+  if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return CPD_ERR_CUDA;
+  k_batch<<<ctas, kBatchThreads, smem, st>>>(a, dmax, Rmax, smem);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+}
+
+std::vector<BatchItem> sorted_items(int B, const int64_t* t_off, const int* dims, const int* ranks,
+                                    const int64_t* w_off, const int64_t* l_off) {
+  std::vector<BatchItem> items((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    BatchItem& it = items[(size_t)b];
+    it.t_off = t_off[b]; it.w_off = w_off[b]; it.l_off = l_off[b];
+    it.d[0] = dims[3 * b]; it.d[1] = dims[3 * b + 1]; it.d[2] = dims[3 * b + 2];
+    it.R = ranks[b]; it.b = b; it.pad = 0;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
+    const double cx = (double)x.d[0] * x.d[1] * x.d[2] * (x.d[0] + x.d[1] + x.d[2]) + 4e3 * x.R * x.R;
+    const double cy = (double)y.d[0] * y.d[1] * y.d[2] * (y.d[0] + y.d[1] + y.d[2]) + 4e3 * y.R * y.R;
+    return cx > cy;
+  });
+  return items;
+}
+
+// mode 0: plain method + network inputs and training targets; mode 1: learned start.
+int batch_ex(int mode, int B, const float* T_packed, const int64_t* t_off, const int* dims, const int* ranks,
+             const cpd_options* opts, const float* params, float* W_packed, const int64_t* w_off,
+             float* lam_packed, const int64_t* l_off, float* X, float* target, float* tmask, cpd_info* infos,
+             void* workspace, size_t ws_bytes, void* stream) {
+  cpd_options o; cpd_default_options(&o);
+  if (opts) o = *opts;
+  o.compress = 1; o.init = CPD_INIT_MLSVD;
+  int dmax = 0, Rmax = 0;
+  int v = batch_validate(B, dims, ranks, o, &dmax, &Rmax);
+  if (v != CPD_OK) return v;
+  if (!T_packed || !t_off || !W_packed || !w_off || !lam_packed || !l_off || !workspace)
+    return CPD_ERR_INVALID_ARG;
+  const size_t smem = batch_smem_bytes(dmax, Rmax, 1);
+  if (smem > smem_cap()) return CPD_ERR_UNSUPPORTED;
+  const ExLayout e = batch_ex_layout(B, dmax, Rmax, o, smem);
+  if (ws_bytes < e.total) return CPD_ERR_WORKSPACE;
+  const std::vector<BatchItem> items = sorted_items(B, t_off, dims, ranks, w_off, l_off);
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(ws + e.p.items, items.data(), sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return CPD_ERR_CUDA;
+  BatchArgs a{};
+  a.T = T_packed; a.W = W_packed; a.lam = lam_packed;
+  a.items = reinterpret_cast<const BatchItem*>(ws + e.p.items);
+  a.B = B;
+  a.queue = reinterpret_cast<int*>(ws + e.p.queue);
+  a.infos = reinterpret_cast<cpd_info*>(ws + e.p.infos);
+  a.scratch = reinterpret_cast<float*>(ws + e.p.scratch);
+  a.scratch_floats_per_cta = e.p.per_cta;
+  a.hist = reinterpret_cast<double*>(ws + e.p.hist);
+  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
+  a.mlsvd_tol = o.mlsvd_tol; a.compress = 1; a.seed = o.seed; a.ctas = e.p.ctas;
+  a.store = reinterpret_cast<float*>(ws + e.store);
+  a.store_floats = e.store_floats;
+  float* Xw = (mode == 1 || X == nullptr) ? reinterpret_cast<float*>(ws + e.X) : X;
+  float* Yw = reinterpret_cast<float*>(ws + e.Y);
+  {
+    ProfScope ps(st, "batch_compress");
+    a.phase = 1; a.X = Xw; a.init = CPD_INIT_MLSVD;
+    if ((v = launch_k_batch(a, dmax, Rmax, smem, e.p.ctas, st)) != CPD_OK) return v;
+  }
+  if (mode == 1) {
+    ProfScope ps(st, "initnet_forward");
+    if (initnet_forward(params, Xw, B, ws + e.act, Yw, st) != cudaSuccess) return CPD_ERR_CUDA;
+  }
+  {
+    ProfScope ps(st, "batch_solve");
+    a.phase = 2; a.X = nullptr;
+    a.init = mode == 1 ? CPD_INIT_LEARNED : CPD_INIT_MLSVD;
+    a.Y = mode == 1 ? Yw : nullptr;
+    a.target = mode == 0 ? target : nullptr;
+    a.tmask = mode == 0 ? tmask : nullptr;
+    if ((v = launch_k_batch(a, dmax, Rmax, smem, e.p.ctas, st)) != CPD_OK) return v;
+  }
+  if (infos) {
+    if (cudaMemcpyAsync(infos, ws + e.p.infos, sizeof(cpd_info) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return CPD_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t cpd_batch_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts) {
@@ -442,6 +714,35 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
       return CPD_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+}
+
+size_t cpd_batch_ex_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts) {
+  cpd_options o; cpd_default_options(&o);
+  if (opts) o = *opts;
+  o.compress = 1; o.init = CPD_INIT_MLSVD;
+  int dmax = 0, Rmax = 0;
+  if (batch_validate(B, dims, ranks, o, &dmax, &Rmax) != CPD_OK) return 0;
+  const size_t smem = batch_smem_bytes(dmax, Rmax, 1);
+  return batch_ex_layout(B, dmax, Rmax, o, smem).total;
+}
+
+int cpd_batch_initnet_data(int B, const float* T_packed, const int64_t* t_off, const int* dims,
+                           const int* ranks, const cpd_options* opts, float* W_packed,
+                           const int64_t* w_off, float* lam_packed, const int64_t* l_off,
+                           float* X, float* target, float* mask, cpd_info* infos,
+                           void* workspace, size_t ws_bytes, void* stream) {
+  return batch_ex(0, B, T_packed, t_off, dims, ranks, opts, nullptr, W_packed, w_off, lam_packed, l_off, X,
+                  target, mask, infos, workspace, ws_bytes, stream);
+}
+
+int cpd_batch_solve_learned(int B, const float* T_packed, const int64_t* t_off, const int* dims,
+                            const int* ranks, const cpd_options* opts, const float* params,
+                            float* W_packed, const int64_t* w_off, float* lam_packed,
+                            const int64_t* l_off, cpd_info* infos, void* workspace,
+                            size_t ws_bytes, void* stream) {
+  if (params == nullptr) return CPD_ERR_INVALID_ARG;
+  return batch_ex(1, B, T_packed, t_off, dims, ranks, opts, params, W_packed, w_off, lam_packed, l_off, nullptr,
+                  nullptr, nullptr, infos, workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

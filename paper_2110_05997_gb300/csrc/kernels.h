@@ -91,6 +91,20 @@ cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float*
                                 size_t scratch_bytes, cudaStream_t st);
 size_t gram_bf16_tc_scratch_bytes(long long I, long long C);
 bool gram_bf16_tc_supported(long long I, const float* T);
+// D(m, n) = epilogue(sum_k A(m, k) B(n, k)) on BF16 tensor cores (FP32 operands
+// rounded on load, FP32 accumulation); A(m, k) = A[m sam + k sak],
+// B(n, k) = B[n sbn + k sbk]; epilogue: + bias[n], ReLU, x [mask(m, n) > 0],
+// D[m ldd + n] = or += (accumulate).
+struct GemmArgs {
+  const float* A; long long sam, sak;
+  const float* B; long long sbn, sbk;
+  float* D; long long ldd;
+  const float* bias;
+  const float* mask; long long ldm;
+  int M, N, K, relu, accumulate;
+};
+cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t st);
+
 struct EigArgs {
   const float* G;             // I x I
   int I, P;                   // P = min(I, R) leading eigenpairs
@@ -189,8 +203,25 @@ struct BatchArgs {
   int compress, init;
   uint64_t seed;
   int ctas;
+  // phased runs around the learned initialiser (0 = the whole method in one pass)
+  int phase;                  // 1: compress and store; 2: solve from the store
+  float* store;               // per-item store, store_floats each (caller's order)
+  size_t store_floats;
+  float* X;                   // phase 1: network input rows (B x CPD_INITNET_IN_PAD) or null
+  const float* Y;             // phase 2: network outputs (B x CPD_INITNET_OUT) for CPD_INIT_LEARNED
+  float* target;              // phase 2: training targets (B x CPD_INITNET_OUT) or null
+  float* tmask;               // phase 2: their masks or null
 };
 size_t batch_smem_bytes(int dmax, int Rmax, int compress);
+size_t batch_store_floats(int dmax, int Rmax);
+// learned initialiser network (initnet.cu)
+size_t initnet_param_count();
+size_t initnet_act_bytes(int B);
+cudaError_t initnet_forward(const float* P, const float* X, int B, void* ws, float* y, cudaStream_t st);
+cudaError_t initnet_grad(const float* P, const float* X, const float* t, const float* mask, int B, void* ws,
+                         float* G, double* loss_out, cudaStream_t st);
+cudaError_t initnet_adam(float* P, float* m, float* v, const float* G, int step, double lr, double b1, double b2,
+                         double eps, cudaStream_t st);
 size_t batch_scratch_floats(int dmax, int Rmax);
 cudaError_t launch_batch(const BatchArgs& a, int threads, size_t smem, cudaStream_t st);
 

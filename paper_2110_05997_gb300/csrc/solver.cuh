@@ -42,7 +42,7 @@ struct State {
 };
 
 struct DevResult {
-  int status, iters, stop, cg_total, kglob, pad0;
+  int status, iters, stop, cg_total, kglob, pad0;   // pad0: start taken (1 = learned factors)
   double rel_err, mu, grad_inf, normS;
 };
 

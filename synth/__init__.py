@@ -131,6 +131,32 @@ def c4_batch(seed: int = SEED_BASE + 4, B: int = 4096, lo: int = 8, hi: int = 48
     return items
 
 
+def c5_initnet(seed: int = SEED_BASE + 5, B: int = 4096, n: int = 16, rlo: int = 1, rhi: int = 8,
+               rho_max: float = 0.9, eta: float = 1e-6):
+    """B planted n x n x n FP32 tensors for the learned initialiser: rank
+    uniform in [rlo, rhi], pairwise collinearity rho uniform in [0, rho_max]
+    per item, noise eta relative.  Returns the packed column-major tensors
+    (B x n^3), ranks and rhos.  Items of one rank are drawn together."""
+    g = rng(seed)
+    Rs = g.integers(rlo, rhi + 1, size=B)
+    rhos = g.uniform(0.0, rho_max, size=B)
+    out = np.empty((B, n ** 3), dtype=np.float32)
+    for R in range(rlo, rhi + 1):
+        idx = np.nonzero(Rs == R)[0]
+        if idx.size == 0:
+            continue
+        Bg = idx.size
+        sr = np.sqrt(rhos[idx])[:, None, None]
+        cr = np.sqrt(1.0 - rhos[idx])[:, None, None]
+        F = [sr * g.standard_normal((Bg, n, 1)) + cr * g.standard_normal((Bg, n, R)) for _ in range(3)]
+        # column-major flattening: entry (i, j, k) at i + n j + n^2 k
+        T0 = np.einsum("bkr,bjr,bir->bkji", F[2], F[1], F[0]).reshape(Bg, -1)
+        E = g.standard_normal(T0.shape)
+        scale = eta * np.linalg.norm(T0, axis=1) / np.linalg.norm(E, axis=1)
+        out[idx] = (T0 + scale[:, None] * E).astype(np.float32)
+    return out, Rs.astype(int), rhos
+
+
 def warming_up_tensor() -> np.ndarray:
     """The 6×5×4 tensor t_ijk = phi(x_i, y_j, z_k) of Sec. 4.2 ("Warming up"),
     phi(x,y,z) = cos(1-x)sin(1+y^2) - sin(1+x^2)e^{x^2+y^2+z^2} - cos(x)ln(1+z),
