@@ -264,6 +264,8 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     if args.workload == "batch":
         return run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush)
+    if args.workload == "initnet":
+        return run_initnet_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush)
     T, R = workload()
     dims = T.shape
     T_flat = synth.flat(T)
@@ -408,6 +410,79 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
     return 0
 
 
+def run_initnet_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush):
+    """Optional line: the learned initialiser.  Trains the network with the
+    library's kernels on the cores of 196608 planted 16^3 problems (rank
+    U{1..8}, collinearity U[0, 0.9], noise 1e-6) solved by the method, then
+    times 4096 held-out problems solved from the learned start (MLSVD start
+    as fallback) and from the MLSVD start alone; reports both, with mean dGN
+    iterations and the fraction reaching the noise floor."""
+    from paper_2110_05997_gb300 import initnet
+
+    def pack(Tc, Rs):
+        B = Tc.shape[0]
+        return (torch.from_numpy(np.ascontiguousarray(Tc.reshape(-1))).to(dev), [b * 4096 for b in range(B)],
+                [[16, 16, 16]] * B, [int(r) for r in Rs])
+    t0 = time.perf_counter()
+    Xs, Ms = [], []
+    for c in range(12):
+        Tc, Rs, _ = synth.c5_initnet(seed=synth.SEED_BASE + 500 + c, B=16384)
+        Tp, to, d, r = pack(Tc, Rs)
+        X, _, msk, *_ = cpd.cpd_batch_initnet_data(Tp, to, d, r, cpd.cpd_default_options(seed=1))
+        Xs.append(X); Ms.append(msk)
+    X, M = torch.cat(Xs), torch.cat(Ms)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    params = initnet.init_params(seed=3, device=dev)
+    t0 = time.perf_counter()
+    hist = initnet.train(params, X, None, M, epochs=20, batch=512, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, M, Xs, Ms
+    Th, Rh, _ = synth.c5_initnet(seed=synth.SEED_BASE + 5, B=4096)
+    Tp, to, d, r = pack(Th, Rh)
+    opts = cpd.cpd_default_options(seed=7)
+    ws = torch.empty(cpd.cpd_batch_ex_workspace_size(d, r, opts), dtype=torch.uint8, device=dev)
+
+    def plain():
+        return cpd.cpd_batch_solve(Tp, to, d, r, opts, stream=stream, workspace=ws, want_infos=False)
+
+    def learned():
+        return cpd.cpd_batch_solve_learned(Tp, to, d, r, params, opts, stream=stream, workspace=ws,
+                                           want_infos=False)
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("plain", plain), ("learned", learned)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            l0 = cpd.cpd_launch_count()
+            with ClockSampler(local_rank) as clk:
+                ms, _ = _timed_steps(torch, fn, flush, stream, args.steps)
+            res[name] = dict(ms=ms / args.steps, launches=cpd.cpd_launch_count() - l0, clocks=clk.summary())
+    _, _, _, _, ib = cpd.cpd_batch_solve(Tp, to, d, r, opts, workspace=ws)
+    _, _, _, _, il = cpd.cpd_batch_solve_learned(Tp, to, d, r, params, opts, workspace=ws)
+    if rank != 0:
+        return 0
+    stats = {}
+    for name, inf in (("plain", ib), ("learned", il)):
+        it = np.array([i["iters"] for i in inf]); e = np.array([i["rel_err"] for i in inf])
+        stats[name] = dict(cpds_per_s=4096 / (res[name]["ms"] * 1e-3), ms_per_batch=res[name]["ms"],
+                           mean_dgn_iters=float(it.mean()), converged_rel_err_lt_1e_5=float(np.mean(e < 1e-5)))
+    stats["learned"]["learned_start_taken"] = float(np.mean([i["init_used"] for i in il]))
+    line = dict(metric="CPDs/sec (batched 16^3 cores, learned start)", value=world * stats["learned"]["cpds_per_s"],
+                unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=res["learned"]["ms"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="bf16 network, f32 dGN", data="synthetic",
+                config=dict(workload="initnet_16^3_r1-8_rho0-0.9_noise1e-6", global_batch=4096 * world,
+                            train_problems=196608, train_epochs=20, l2="flushed between steps (256 MB write)"),
+                plain=stats["plain"], learned=stats["learned"], train_loss_first_last=[hist[0], hist[-1]],
+                data_s=t_data, train_s=t_train, gpu_launches=int(res["learned"]["launches"]),
+                clocks=res["learned"]["clocks"])
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,7 +490,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gram", choices=["fp32", "bf16"], default="bf16")
-    ap.add_argument("--workload", choices=["compressed", "batch"], default="compressed")
+    ap.add_argument("--workload", choices=["compressed", "batch", "initnet"], default="compressed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -8,7 +8,7 @@
  * ---------------------------------------
  *  - Tensors are dense and column-major: entry (i1, ..., iL) (0-based) sits at
  *    i1 + I1*(i2 + I2*(i3 + ...)), i.e. i1 fastest, the order in which the
- *    thesis unfolds tensors (Sec. 1.2, Algorithm "Unfolding").
+ *    thesis unfolds tensors (Sec. 2.1.1, Algorithm "Unfolding").
  *  - A CPD with factors W^(l) (I_l x R, column-major) is passed as ONE buffer
  *    holding vec(W^(1)), ..., vec(W^(L)) back to back: the stacked parameter
  *    vector w of Sec. 3.1.  Block l starts at R * (I_1 + ... + I_{l-1}).
@@ -68,9 +68,10 @@ typedef enum {
   CPD_INIT_MLSVD = 0,   /* R core entries of largest |s| as rank-one terms          */
   CPD_INIT_RANDOM = 1,  /* N(0,1) by Box-Muller on SplitMix64 stream 2 of `seed`    */
   CPD_INIT_GIVEN = 2,   /* caller's W0 in the ORIGINAL space (projected under compression) */
-  CPD_INIT_LEARNED = 3  /* the learned initialiser's factors for the core, or the MLSVD
-                           start when that has the smaller residual (batched solver
-                           only: cpd_batch_solve_learned; no counterpart in the thesis) */
+  CPD_INIT_LEARNED = 3  /* the learned initialiser's factors for the core when their
+                           residual is below half the MLSVD start's, else the MLSVD
+                           start (batched solver only: cpd_batch_solve_learned; no
+                           counterpart in the thesis) */
 } cpd_init;
 
 /* Arithmetic of the compression Gram matrices. */
@@ -151,7 +152,7 @@ int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_op
  * compression (if opts->compress), initialisation, damped Gauss-Newton on the
  * core (Sec. 4.1.3: residual, MTTKRP gradient, Hadamard-of-Gram Pi matrices,
  * matrix-free J^T J v of Theorem "Hv" inside Jacobi-preconditioned CG with the
- * diagonal regulariser of Sec. 4.7), uncompression (Sec. 4.1.4), optional
+ * diagonal regulariser of Sec. 4.8), uncompression (Sec. 4.1.4), optional
  * refinement iterations on T, and output normalisation.
  *   T          device, element type `dtype` (CPD_F64 only with compress = 0)
  *   W0         device, FP32, stacked I_l x R blocks (INIT_GIVEN), else NULL
@@ -214,7 +215,7 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
  * No counterpart in the thesis, which starts dGN from random factors or from
  * the compressed core (Sec. 4.1.2): a multilayer perceptron proposes the
  * initial factors for dGN on a compressed core, and the solver keeps the
- * MLSVD start whenever that has the smaller residual.
+ * MLSVD start unless the proposal's residual is below half of its residual.
  *
  *   input row x (CPD_INITNET_IN_PAD floats): S / ||S|| with S the core
  *     (I1 x I2 x I3 <= 16^3) zero-padded into a 16 x 16 x 16 column-major
@@ -272,7 +273,8 @@ int cpd_initnet_adam(float* params, float* m, float* v, const float* grad, int s
  *    exist: rows below the core dims, columns below R; all 0 for ineligible items).
  *    X, target, mask: device, row-major; any of them may be NULL.
  *  cpd_batch_solve_learned: the network (params) proposes each eligible
- *    item's start; cpd_info.init_used tells which start dGN took.
+ *    item's start, taken when its residual is below half the MLSVD start's;
+ *    cpd_info.init_used tells which start dGN took.
  */
 size_t cpd_batch_ex_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts);
 int cpd_batch_initnet_data(int B, const float* T_packed, const int64_t* t_off, const int* dims,
@@ -313,7 +315,7 @@ int cpd_core_eval(const float* S, int L, const int64_t* dims, int R, const float
                   size_t ws_bytes, void* stream);
 
 /*
- * cpd_jtj_apply — out = J^T J v for the CPD W (Theorem "Hv", Sec. 3.3.2):
+ * cpd_jtj_apply — out = J^T J v for the CPD W (Theorem "Hv", Sec. 3.5.3):
  *   block l' of out = V^(l') Pi^(l') + sum_{l''≠l'} W^(l') (Pi^(l',l'') * (V^(l'')^T W^(l''))).
  *   W, V, out device FP32 stacked blocks.
  */

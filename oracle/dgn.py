@@ -1,10 +1,10 @@
-"""Damped Gauss-Newton CPD (thesis Ch. 3, Sec. 4.1.2-4.1.4, Sec. 4.7), FP64.
+"""Damped Gauss-Newton CPD (thesis Ch. 3, Sec. 4.1.2-4.1.4, Sec. 4.8), FP64.
 
 Notation follows the thesis: W^(l) (I_l × R) factor matrices, w their stacked
 vec (Sec. 3.1), f the residual (eq. (residual_function)), F = ½||f||^2,
-A = J_f, b = -f, pi^(l) = W^(l)T W^(l) (Sec. 3.3.2), Pi^(l',l'') and Pi^(l')
+A = J_f, b = -f, pi^(l) = W^(l)T W^(l) (Sec. 3.5.3), Pi^(l',l'') and Pi^(l')
 Hadamard products of the other modes' Grams, D the diagonal regulariser and
-M the Jacobi preconditioner (Sec. 4.7).
+M the Jacobi preconditioner (Sec. 4.8).
 
 Readings of passages that are silent, garbled or inconsistent (each is
 listed with its justification in the design notes):
@@ -18,14 +18,14 @@ listed with its justification in the design notes):
       so that powers that are integers in exact arithmetic do not round up;
   R4  the CG stop test is ||r||^2 < tol, absolute, tol the dGN tolerance;
   R5  the gain ratio uses ½||f + Jx||^2 = F - <g, x> + ½<x, J^T J x>, g = -grad F
-      (exact; Sec. 3.3.1 gain ratio with consistent ½ factors);
+      (exact; Sec. 3.5.2 gain ratio with consistent ½ factors);
   R6  per iteration: solve -> w += x -> norm-balance (keeps column signs; the
       common norm is the geometric mean) -> new residual and gradient ->
       gain ratio -> mu update (x3 below 0.25, /3 above 0.75) -> stop tests;
       the starting point is balanced too;
   R7  D and M are rebuilt every iteration from the current balanced factors;
       for general L, gamma_r^(l) = prod_{j≠l}||w_r^(j)|| ·
-      max_m max_r' prod_{j≠m}||w_r'^(j)|| (the L = 3 formulas of Sec. 4.7);
+      max_m max_r' prod_{j≠m}||w_r'^(j)|| (the L = 3 formulas of Sec. 4.8);
   R8  stop tests in the printed order; the gradient-norm test uses the
       gradient at the new iterate; tests 5 and 6 run when k is a multiple of
       c = 1 + ceil(maxiter/10) and k > 2c, with the printed windows; the
@@ -98,7 +98,7 @@ def cg_maxiter(k: int, seed: int, a: float = 0.4, b: float = 0.9) -> int:
     return lo + splitmix64(seed, STREAM_CG, k) % (hi - lo + 1)
 
 
-# --- residual, gradient, Grams, Hv (Sec. 3.3, Sec. 4.1.3) --------------------
+# --- residual, gradient, Grams, Hv (Sec. 3.5, Sec. 4.1.3) --------------------
 
 def residual(T: np.ndarray, Ws) -> np.ndarray:
     """f_{i1..iL} = t_{i1..iL} - sum_r prod_l w_{il r}^(l)  (eq. (residual_function))."""
@@ -113,13 +113,13 @@ def neg_gradient(f: np.ndarray, Ws):
 
 
 def grams(Ws):
-    """pi^(l) = W^(l)T W^(l)  (Sec. 3.3.2)."""
+    """pi^(l) = W^(l)T W^(l)  (Sec. 3.5.3)."""
     return [W.T @ W for W in Ws]
 
 
 def pi_matrices(gr):
     """Pi^(l',l'') = Hadamard product of pi^(l) over l ∉ {l', l''}, and
-    Pi^(l') = Hadamard product over l ≠ l'  (Sec. 3.3.2)."""
+    Pi^(l') = Hadamard product over l ≠ l'  (Sec. 3.5.3)."""
     L = len(gr)
     R = gr[0].shape[0]
     Pi1 = []
@@ -143,7 +143,7 @@ def pi_matrices(gr):
 
 
 def jtj_apply(Ws, Pi1, Pi2, Vs):
-    """Theorem "Hv" (Sec. 3.3.2): block l' of J^T J·v is
+    """Theorem "Hv" (Sec. 3.5.3): block l' of J^T J·v is
     V^(l')Pi^(l') + sum_{l''≠l'} W^(l')·(Pi^(l',l'') * (V^(l'')T W^(l'')))."""
     L = len(Ws)
     out = []
@@ -161,7 +161,7 @@ def column_norms(Ws):
 
 
 def regularizer(Ws):
-    """gamma_r^(l) of Sec. 4.7 (reading R7 for general L)."""
+    """gamma_r^(l) of Sec. 4.8 (reading R7 for general L)."""
     L = len(Ws)
     nr = column_norms(Ws)
     prod_other = []
@@ -177,7 +177,7 @@ def regularizer(Ws):
 
 def preconditioner(Ws, gamma, mu: float):
     """M = diag(a_ii + mu·d_ii): block (l, r) is prod_{j≠l}||w_r^(j)||^2 + mu·gamma_r^(l)
-    (Sec. 4.7, D_X, D_Y, D_Z and the general-L diagonal of J^T J)."""
+    (Sec. 4.8, D_X, D_Y, D_Z and the general-L diagonal of J^T J)."""
     L = len(Ws)
     nr = column_norms(Ws)
     out = []

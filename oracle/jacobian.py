@@ -1,6 +1,6 @@
 """Explicit Jacobian of the CPD residual, for tests on tiny sizes only.
 
-Built entry by entry from Lemma "partialf" (Sec. 3.2): the derivative of
+Built entry by entry from Lemma "partialf" (Sec. 3.4): the derivative of
 f_{i1..iL} with respect to w_{i' r'}^(l') is -prod_{l≠l'} w_{il r'}^(l) when
 i' = i_l', else 0.  Rows are the entries of T in column-major order (the
 row order does not change J^T J or J^T f); columns follow the stacked vec

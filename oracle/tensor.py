@@ -2,8 +2,8 @@
 
 Conventions fixed by the thesis and used everywhere:
   * unfolding T_(l): rows indexed by i_l, columns ordered with i_1 fastest
-    (skipping l) -- Algorithm "Unfolding" (Sec. 1.2) and its 3×4×2 example;
-  * mode-l product S = T ×_l M: S_(l) = M · T_(l) (Sec. 1.2 definition and
+    (skipping l) -- Algorithm "Unfolding" (Sec. 2.1.1) and its 3×4×2 example;
+  * mode-l product S = T ×_l M: S_(l) = M · T_(l) (Sec. 2.1 definition and
     its example with M = [[1,3,5],[2,4,6]]);
   * multilinear multiplication (M1,...,ML)·T = T ×_1 M1 ... ×_L ML;
   * Kronecker product A ⊗ B with B's index fastest, Khatri-Rao product

@@ -328,6 +328,16 @@ def cpd_batch_workspace_size(dims, ranks, opts: cpd_options | None = None) -> in
     return int(lib().cpd_batch_workspace_size(B, d, r, C.byref(opts)))
 
 
+def cpd_batch_ex_workspace_size(dims, ranks, opts: cpd_options | None = None) -> int:
+    """Workspace bytes of cpd_batch_initnet_data / cpd_batch_solve_learned
+    (also enough for cpd_batch_solve on the same items)."""
+    opts = opts or cpd_default_options()
+    B = len(ranks)
+    d = (C.c_int * (3 * B))(*[int(x) for row in dims for x in row])
+    r = (C.c_int * B)(*[int(x) for x in ranks])
+    return int(lib().cpd_batch_ex_workspace_size(B, d, r, C.byref(opts)))
+
+
 def cpd_batch_solve(T_packed, t_off, dims, ranks, opts: cpd_options | None = None, stream=None,
                     workspace=None, want_infos: bool = True):
     """B third-order CPDs in one persistent launch.  ``T_packed`` holds the
@@ -388,7 +398,7 @@ def cpd_batch_initnet_data(T_packed, t_off, dims, ranks, opts: cpd_options | Non
     msk = torch.empty(B, INITNET_OUT, dtype=torch.float32, device=dev)
     infos = (cpd_info * B)()
     if workspace is None:
-        workspace = _workspace(int(lib().cpd_batch_ex_workspace_size(B, d, r, C.byref(opts))), dev)
+        workspace = _workspace(cpd_batch_ex_workspace_size(dims, ranks, opts), dev)
     st = lib().cpd_batch_initnet_data(B, _ptr(T_packed), to, d, r, C.byref(opts), _ptr(W), wof, _ptr(lam), lof,
                                       _ptr(X), _ptr(tgt), _ptr(msk), infos, _ptr(workspace), workspace.numel(),
                                       _stream(stream))
@@ -404,7 +414,7 @@ def cpd_batch_solve_learned(T_packed, t_off, dims, ranks, params, opts: cpd_opti
     B, dev, W, lam, w_off, l_off, d, r, to, wof, lof = _batch_marshal(T_packed, t_off, dims, ranks)
     infos = (cpd_info * B)() if want_infos else None
     if workspace is None:
-        workspace = _workspace(int(lib().cpd_batch_ex_workspace_size(B, d, r, C.byref(opts))), dev)
+        workspace = _workspace(cpd_batch_ex_workspace_size(dims, ranks, opts), dev)
     st = lib().cpd_batch_solve_learned(B, _ptr(T_packed), to, d, r, C.byref(opts), _ptr(params), _ptr(W), wof,
                                        _ptr(lam), lof, infos, _ptr(workspace), workspace.numel(),
                                        _stream(stream))

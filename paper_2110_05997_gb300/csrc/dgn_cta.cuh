@@ -140,8 +140,10 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
   __shared__ int s_init_used;
   if (a.init == CPD_INIT_LEARNED) {
     // two candidate starts: the MLSVD-energy start and the network's factors
-    // (a.W0); dGN starts from the one with the smaller residual (the MLSVD
-    // start is the fallback).  a.W_out holds the first candidate meanwhile.
+    // (a.W0); dGN starts from the network's only when its residual is below
+    // half the MLSVD start's (norms; a smaller margin let starts from worse
+    // basins through and cost iterations on the 16^3 workload); the MLSVD
+    // start is the fallback.  a.W_out holds the first candidate meanwhile.
     init_factors<L>(s, b, CPD_INIT_MLSVD, nullptr, a.seed, chosen);
     balance<L>(s, b);
     double f_mlsvd, g_mlsvd;
@@ -150,7 +152,7 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
     init_factors<L>(s, b, CPD_INIT_GIVEN, a.W0, a.seed, chosen);
     balance<L>(s, b);
     core_pass<L>(s, b, fsq, ginf);
-    if (threadIdx.x == 0) s_init_used = (isfinite(fsq) && !(fsq > f_mlsvd)) ? 1 : 0;
+    if (threadIdx.x == 0) s_init_used = (isfinite(fsq) && fsq < 0.25 * f_mlsvd) ? 1 : 0;
     __syncthreads();
     if (!s_init_used) {
       for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] = a.W_out[j];

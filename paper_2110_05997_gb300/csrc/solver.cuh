@@ -1,4 +1,4 @@
-// CTA-level damped Gauss-Newton building blocks (thesis Sec. 3.3, 4.1.3, 4.7).
+// CTA-level damped Gauss-Newton building blocks (thesis Sec. 3.5, 4.1.3, 4.7).
 //
 // Every function here is executed by ALL threads of one CTA; vectors of the
 // parameter space (length n = R * sum I_l, stacked vec blocks of Sec. 3.1)
@@ -57,7 +57,7 @@ __device__ __forceinline__ void decode_j(const Shape& s, int j, int& l, int& i, 
 }
 
 // pi^(l) = W^(l)T W^(l) and the Pi matrices as Hadamard products of the
-// other modes' Grams (Sec. 3.3.2, the display defining Pi^(l',l'') and Pi^(l')).
+// other modes' Grams (Sec. 3.5.3, the display defining Pi^(l',l'') and Pi^(l')).
 template <int L>
 __device__ void grams_pi(const Shape& s, const Bufs& b) {
   const int R = s.R, RR = R * R;
@@ -83,7 +83,7 @@ __device__ void grams_pi(const Shape& s, const Bufs& b) {
   __syncthreads();
 }
 
-// Diagonal regulariser D (gamma) and Jacobi preconditioner M of Sec. 4.7:
+// Diagonal regulariser D (gamma) and Jacobi preconditioner M of Sec. 4.8:
 // gamma_r^(l) = prod_{j!=l}||w_r^(j)|| * max_m max_r' prod_{j!=m}||w_r'^(j)||,
 // M_(l,r) = prod_{j!=l}||w_r^(j)||^2 + mu * gamma_r^(l); msq = M^{-1/2}.
 template <int L>
@@ -406,7 +406,7 @@ __device__ inline void fill_cg_table(int* tab, int len, uint64_t seed, double ca
   __syncthreads();
 }
 
-// Gain ratio (Sec. 3.3.1 / 4.1.3) and the damping update x3 below 0.25,
+// Gain ratio (Sec. 3.5.2 / 4.1.3) and the damping update x3 below 0.25,
 // /3 above 0.75 (the rule Sec. 4.1.3 settles on).
 __device__ inline double gain_update(double F_old, double F_new, double pred_drop, double& mu) {
   const double g = pred_drop > 0.0 ? quick_div(F_old - F_new, pred_drop) : 0.0;

@@ -7,10 +7,10 @@ Gauss-Newton).  Every generator is deterministic in its seed.
 
 Layout contract: a tensor T with dims (I1, ..., IL) is an ``np.ndarray`` of
 that shape whose memory order is column-major (Fortran), i.e. i1 fastest, as
-the thesis fixes for unfoldings and vec (Sec. 1.2, Algorithm "Unfolding";
+the thesis fixes for unfoldings and vec (Sec. 2.1.1, Algorithm "Unfolding";
 Sec. 3.1 for vec of factor matrices).  Factor matrices are Iℓ×R, column-major.
 
-Workload recipes (Sec. 4.3 "Collinear factors" and Sec. 4.2 noise model):
+Workload recipes (Sec. 4.3.5 "Collinear factors" and the noise model of Sec. 4.9.2):
   * planted rank-R tensor T0 = sum_r w_r^(1) ⊗ ... ⊗ w_r^(L) with factor
     columns drawn i.i.d. N(0, I);
   * "pairwise collinearity rho": w_r = sqrt(rho)·s + sqrt(1-rho)·g_r with s, g_r

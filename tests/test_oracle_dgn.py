@@ -31,7 +31,7 @@ def test_gradient_brute_force_and_finite_differences(dims, R):
     f = O.residual(T, Ws)
     g = O.neg_gradient(f, Ws)
     L = len(dims)
-    # Theorem "partialF" written as the brute-force sum of Sec. 3.2 (after Lemma partialf)
+    # Theorem "partialF" written as the brute-force sum of Sec. 3.4 (after Lemma partialf)
     for lp in range(L):
         for ip in range(dims[lp]):
             for rp in range(R):
@@ -103,7 +103,7 @@ def test_jtj_scaling_null_vectors():
 
 
 def test_regularizer_makes_system_diagonally_dominant():
-    # Sec. 4.7: J^T J + D is diagonally dominant; the a_ii part of M is diag(J^T J)
+    # Sec. 4.8: J^T J + D is diagonally dominant; the a_ii part of M is diag(J^T J)
     dims, R = (4, 3, 3), 3
     _, Ws = _rand_problem(dims, R, 4)
     J = explicit_jacobian(Ws)
@@ -184,7 +184,7 @@ def test_balance_keeps_tensor_and_equalises_norms():
 
 
 def test_dgn_descent_and_gain_denominator():
-    # Theorem (dGN) item 2 and the gain-ratio denominator > 0 (Sec. 3.3.1): along a
+    # Theorem (dGN) item 2 and the gain-ratio denominator > 0 (Sec. 3.5.2): along a
     # run, <grad F, x> < 0 and F - ½||f + Jx||^2 = ||Jx||^2 + ... > 0
     T, _ = synth.planted(21, (6, 5, 4), 3, 0.0, 0.01)
     Ws = O.balance(O.init_random(3, T.shape, 3))

@@ -9,7 +9,7 @@ from conftest import read_golden
 
 
 def _example_tensor():
-    # frontal slices of the Sec. 1.2 example: t_ijk = 1 + i + 3j + 12k (0-based)
+    # frontal slices of the Sec. 2.1.1 example: t_ijk = 1 + i + 3j + 12k (0-based)
     T = np.zeros((3, 4, 2))
     for i, j, k in itertools.product(range(3), range(4), range(2)):
         T[i, j, k] = 1 + i + 3 * j + 12 * k
