@@ -237,6 +237,30 @@ def run_reference(args, rank, world):
     return 0
 
 
+def max_over_ranks(ms: float, world: int, device="cpu") -> float:
+    """The slowest rank's timed-region milliseconds; every rank calls it after
+    its own timed region (a barrier, then an all-reduce MAX)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank_step: float, steps: int, world: int, ms: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (ms * 1e-3)
+
+
+def start_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def _timed_steps(torch, step, flush, stream, K):
     """K steps, each bracketed by CUDA events on the launching stream, with an
     L2 flush (256 MB write) between steps outside the events."""
@@ -280,9 +304,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        start_barrier(world)
         torch.cuda.synchronize()
         l0 = cpd.cpd_launch_count()
         with ClockSampler(local_rank) as clk:
@@ -290,13 +312,8 @@ def run_ours(args, rank, world, local_rank):
         launches = cpd.cpd_launch_count() - l0
         W, lam, info, _ = outs[-1]
         infos = [o[2] for o in outs]
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * args.steps / (ms * 1e-3)
+        ms = max_over_ranks(ms, world, dev)
+        value = whole_job_value(1, args.steps, world, ms)
 
         # per-stage device time: a second K-step region with CUDA-event scopes
         # around every launch (direct launches; graphs are bypassed while profiling)
@@ -318,8 +335,10 @@ def run_ours(args, rank, world, local_rank):
             Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
             lh.copy_(lam2, non_blocking=True)
         e2e_step()
+        start_barrier(world)
         e2e_ms, _ = _timed_steps(torch, e2e_step, flush, stream, args.steps)
-    e2e = dict(value=world * args.steps / (e2e_ms * 1e-3), unit=UNIT,
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e = dict(value=whole_job_value(1, args.steps, world, e2e_ms), unit=UNIT,
                h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4))
 
     if rank != 0:
@@ -392,14 +411,17 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
+        start_barrier(world)
+        torch.cuda.synchronize()
         l0 = cpd.cpd_launch_count()
         with ClockSampler(local_rank) as clk:
             ms, _ = _timed_steps(torch, step, flush, stream, args.steps)
         launches = cpd.cpd_launch_count() - l0
+    ms = max_over_ranks(ms, world, dev)
     B = len(items)
     if rank != 0:
         return 0
-    line = dict(metric="CPDs/sec (batched uneven CPDs)", value=world * B * args.steps / (ms * 1e-3),
+    line = dict(metric="CPDs/sec (batched uneven CPDs)", value=whole_job_value(B, args.steps, world, ms),
                 unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload="batch_4096_uneven_3rd_order_r2-8_noise1e-6", global_batch=B * world,
@@ -456,9 +478,12 @@ def run_initnet_workload(args, rank, world, local_rank, torch, cpd, dev, stream,
             for _ in range(args.warmup):
                 fn()
             torch.cuda.synchronize()
+            start_barrier(world)
+            torch.cuda.synchronize()
             l0 = cpd.cpd_launch_count()
             with ClockSampler(local_rank) as clk:
                 ms, _ = _timed_steps(torch, fn, flush, stream, args.steps)
+            ms = max_over_ranks(ms, world, dev)
             res[name] = dict(ms=ms / args.steps, launches=cpd.cpd_launch_count() - l0, clocks=clk.summary())
     _, _, _, _, ib = cpd.cpd_batch_solve(Tp, to, d, r, opts, workspace=ws)
     _, _, _, _, il = cpd.cpd_batch_solve_learned(Tp, to, d, r, params, opts, workspace=ws)
