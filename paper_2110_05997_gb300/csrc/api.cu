@@ -70,9 +70,15 @@ size_t smem_limit() {
   return lim;
 }
 
+// CTA size of the single-CTA solvers: one thread per unknown, rounded up to
+// whole warps (every per-entry phase of the CG then takes one pass; more
+// warps than that only add barrier cost), at least 4 warps, at most 1024.
 int threads_for(const cpd_options* o, int n) {
   if (o && o->block_threads > 0) return o->block_threads;
-  return n > 2048 ? 1024 : 256;
+  int t = (n + 31) / 32 * 32;
+  if (t < 128) t = 128;
+  if (t > 1024) t = 1024;
+  return t;
 }
 
 // Everything the solve needs, carved from the workspace (or sized when base == nullptr).

@@ -15,12 +15,16 @@ struct Shape {
   int L, R, n, N;
   int d[kMaxL];
   int off[kMaxL + 1];   // start of block l in the stacked vector; off[L] = n
+  float dinv[kMaxL];    // 1 / d[l], for index decoding without integer division
 };
 
 __host__ __device__ inline void make_shape(Shape& s, int L, const int* d, int R) {
   s.L = L; s.R = R; s.N = 1; s.off[0] = 0;
-  for (int l = 0; l < kMaxL; ++l) s.d[l] = 1;
-  for (int l = 0; l < L; ++l) { s.d[l] = d[l]; s.N *= d[l]; s.off[l + 1] = s.off[l] + R * d[l]; }
+  for (int l = 0; l < kMaxL; ++l) { s.d[l] = 1; s.dinv[l] = 1.f; }
+  for (int l = 0; l < L; ++l) {
+    s.d[l] = d[l]; s.dinv[l] = 1.f / (float)d[l];
+    s.N *= d[l]; s.off[l + 1] = s.off[l] + R * d[l];
+  }
   s.n = s.off[L];
 }
 
@@ -51,8 +55,11 @@ __device__ __forceinline__ void decode_j(const Shape& s, int j, int& l, int& i, 
   l = 0;
 #pragma unroll
   for (int t = 1; t < L; ++t) l += (j >= s.off[t]) ? 1 : 0;
+  // q = r d + i with i < d: (q + 0.5) / d is at least 0.5 / d away from an
+  // integer, far more than the FP32 rounding of (q + 0.5) * (1/d) for
+  // q < R d <= 2^16 d, so the floor is exact
   const int q = j - s.off[l];
-  r = q / s.d[l];
+  r = __float2int_rd(((float)q + 0.5f) * s.dinv[l]);
   i = q - r * s.d[l];
 }
 
