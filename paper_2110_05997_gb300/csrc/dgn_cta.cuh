@@ -188,7 +188,7 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
     grams_pi<L>(s, b);                         // its first barrier publishes s_maxit
     regularize<L>(s, b, mu);
     const int maxit = s_maxit;
-    const int its = pcg<L>(s, b, mu, maxit, a.tol);
+    const int its = (s.n <= (int)blockDim.x) ? pcg_owned<L>(s, b, mu, maxit, a.tol) : pcg<L>(s, b, mu, maxit, a.tol);
     double pred_drop, step;
     finish_step<L>(s, b, pred_drop, step);
     core_pass<L>(s, b, fsq, ginf);

@@ -221,6 +221,68 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
   return its;
 }
 
+// The same PCG when every thread owns at most one unknown (n <= blockDim.x):
+// x, r, p, the preconditioner entry and the decoded index stay in registers
+// and only M^{-1/2} p (the vector J^T J is applied to) goes through shared
+// memory.  Same operations in the same order as pcg(), so the same results.
+template <int L>
+__device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const int n = s.n, R = s.R;
+  const int j = threadIdx.x;
+  const bool own = j < n;
+  int l = 0, i = 0, r = 0;
+  float m = 0.f, mg = 0.f, x = 0.f, rj = 0.f, pj = 0.f;
+  const float muf = (float)mu;
+  float v[1] = {0.f};
+  if (own) {
+    decode_j<L>(s, j, l, i, r);
+    m = b.msq[l * R + r];
+    mg = muf * b.gam[l * R + r];
+    rj = m * b.G[j];
+    pj = rj;
+    b.Tmp[j] = m * rj;
+    v[0] = rj * rj;
+  }
+  double rr0[1];
+  block_sum<1>(v, rr0, b.red);
+  double rr = rr0[0];
+  int its = 0;
+  for (int it = 0; it < maxit; ++it) {
+    hv_xy<L>(s, b, b.Tmp);
+    float pzf[1] = {0.f};
+    float z = 0.f;
+    if (own) {
+      z = m * (hv_entry<L>(s, b, b.Tmp, l, i, r) + mg * (m * pj));
+      pzf[0] = pj * z;
+    }
+    double pz[1];
+    block_sum<1>(pzf, pz, b.red);
+    if (!(pz[0] > 0.0)) break;
+    const double alpha = warp_div(rr, pz[0]);
+    const float af = (float)alpha;
+    float rnf[1] = {0.f};
+    if (own) {
+      x = fmaf(af, pj, x);
+      rj = fmaf(-af, z, rj);
+      rnf[0] = rj * rj;
+    }
+    double rn[1];
+    block_sum<1>(rnf, rn, b.red);
+    const double beta = rr > 0.0 ? warp_div(rn[0], rr) : 0.0;
+    rr = rn[0];
+    its = it + 1;
+    if (own) {
+      pj = fmaf((float)beta, pj, rj);
+      b.Tmp[j] = m * pj;
+    }
+    __syncthreads();
+    if (rr < tol) break;
+  }
+  if (own) b.X[j] = x;
+  __syncthreads();
+  return its;
+}
+
 // Norm-balancing (Sec. 4.1.3 "Updates"): ||w_r^(1)|| = ... = ||w_r^(L)||,
 // common value the geometric mean, signs kept.
 template <int L>
