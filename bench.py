@@ -419,6 +419,33 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
         launches = cpd.cpd_launch_count() - l0
     ms = max_over_ranks(ms, world, dev)
     B = len(items)
+    # what the autotuner chose between: each CTA size forced, one timed step
+    cta_ms = {}
+    for th in (64, 128, 256):
+        o_th = cpd.cpd_default_options(block_threads=th)
+        with torch.cuda.stream(stream):
+            cpd.cpd_batch_solve(Tp, offs, dims, ranks, o_th, stream=stream, workspace=ws, want_infos=False)
+            torch.cuda.synchronize()
+            t_th, _ = _timed_steps(torch, lambda: cpd.cpd_batch_solve(Tp, offs, dims, ranks, o_th, stream=stream,
+                                                                      workspace=ws, want_infos=False),
+                                   flush, stream, 2)
+        cta_ms[str(th)] = t_th / 2
+    # the same problems one launch sequence per tensor (cpd_dgn_solve, graph
+    # replays), on a seeded sample of 256 items
+    pick = np.random.default_rng(7).choice(B, size=min(256, B), replace=False)
+    per = [(torch.from_numpy(synth.flat(items[int(b)]["T"]).astype(np.float32)).to(dev), dims[int(b)],
+            ranks[int(b)]) for b in pick]
+    popts = cpd.cpd_default_options()
+    pws = torch.empty(max(cpd.cpd_workspace_size(d, r, popts) for _, d, r in per), dtype=torch.uint8, device=dev)
+
+    def per_tensor():
+        for Tb, d, r in per:
+            cpd.cpd_dgn_solve(Tb, d, r, popts, stream=stream, workspace=pws)
+    with torch.cuda.stream(stream):
+        per_tensor()
+        torch.cuda.synchronize()
+        pms, _ = _timed_steps(torch, per_tensor, flush, stream, 1)
+    per_rate = len(per) / (pms * 1e-3)
     if rank != 0:
         return 0
     line = dict(metric="CPDs/sec (batched uneven CPDs)", value=whole_job_value(B, args.steps, world, ms),
@@ -427,7 +454,10 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
                 config=dict(workload="batch_4096_uneven_3rd_order_r2-8_noise1e-6", global_batch=B * world,
                             parallelism=f"one persistent launch per GPU x{world}",
                             l2="flushed between steps (256 MB write)"),
-                gpu_launches=int(launches), clocks=clk.summary())
+                gpu_launches=int(launches), clocks=clk.summary(),
+                ms_per_batch_by_cta_threads=cta_ms,
+                per_tensor_launches=dict(cpds_per_s=per_rate, sample=f"{len(per)} seeded items of the batch, "
+                                         "one cpd_dgn_solve (graph replay) each", per_gpu=True))
     print(json.dumps(line), flush=True)
     return 0
 

@@ -203,7 +203,14 @@ int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int64_t* dims, 
  *   lam_packed device, FP32 outputs: item b's R_b weights at offset l_off[b]
  *   infos      host, B records (synchronises the stream) or NULL
  * The per-item options are `opts` (compress, init MLSVD/RANDOM, tolerances);
- * item b uses seed opts->seed + b.
+ * item b uses seed opts->seed + b.  opts->block_threads of 64, 128 or 256
+ * fixes the CTA size (and with it the Gram tile shape and CTAs per SM);
+ * otherwise an autotuner times the three on the first call for a shape class
+ * (device, largest mode, largest rank, compression, batch size rounded to a
+ * power of two), keeps the fastest, and later calls use it (the first call
+ * therefore runs the batch four times).  On a non-default stream that is not
+ * being captured, the item upload, queue reset and launch are captured once
+ * per argument set into a CUDA graph and replayed.
  */
 size_t cpd_batch_workspace_size(int B, const int* dims, const int* ranks, const cpd_options* opts);
 int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const int* dims,

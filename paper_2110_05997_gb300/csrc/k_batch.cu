@@ -6,6 +6,8 @@
 // (Sec. 4.1.2-4.1.3, the same device code as the single-tensor solver),
 // uncompression (Sec. 4.1.4) and output normalisation.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string.h>
 #include <vector>
 
@@ -16,22 +18,26 @@
 
 namespace cpdk {
 
-constexpr int kBatchThreads = 128;
+constexpr int kBatchThreadChoices[3] = {64, 128, 256};   // CTA sizes the autotuner times
 constexpr int kBatchMaxDim = 64;
 constexpr int kBatchMaxRank = 16;
 constexpr int kGTile = 16;           // rows of the Gram's staging tile
 constexpr int kGLd = 68;             // padded row length of the staging tile
 
 // G (b x b, column-major) = sum_q X[q,:]^T X[q,:] with X[q, j] = T[i + a j + a b k],
-// q = i + a k over the a*c "other" indices.  b <= 64; 128 threads, each a
-// 4 x 8 block of the 64 x 64 output; rows of X staged in shared memory.
+// q = i + a k over the a*c "other" indices.  b <= 64; TH threads, each a
+// TM x TN block of the 64 x 64 output (TH = 64: 8 x 8, 128: 4 x 8, 256: 4 x 4,
+// the tile shapes the batch autotuner chooses between); rows of X staged in
+// shared memory.
+template <int TH>
 __device__ void cta_gram(const float* __restrict__ T, int a, int b, int c, float* G, float* tile) {
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-  float acc[4][8];
+  constexpr int TN = TH == 256 ? 4 : 8, NCG = 64 / TN, TM = 64 / (TH / NCG);
+  const int tx = threadIdx.x % NCG, ty = threadIdx.x / NCG;
+  float acc[TM][TN];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < TM; ++u)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
   const long long K = (long long)a * c;
   for (long long qb = 0; qb < K; qb += kGTile) {
     for (int e = threadIdx.x; e < kGTile * 64; e += blockDim.x) {
@@ -47,23 +53,29 @@ __device__ void cta_gram(const float* __restrict__ T, int a, int b, int c, float
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kGTile; ++kk) {
-      const float4 ar = *reinterpret_cast<const float4*>(tile + kk * kGLd + ty * 4);
-      const float4 b0 = *reinterpret_cast<const float4*>(tile + kk * kGLd + tx * 8);
-      const float4 b1 = *reinterpret_cast<const float4*>(tile + kk * kGLd + tx * 8 + 4);
-      const float av[4] = {ar.x, ar.y, ar.z, ar.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      float av[TM], bv[TN];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < TM; u += 4) {
+        const float4 ar = *reinterpret_cast<const float4*>(tile + kk * kGLd + ty * TM + u);
+        av[u] = ar.x; av[u + 1] = ar.y; av[u + 2] = ar.z; av[u + 3] = ar.w;
+      }
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+      for (int v = 0; v < TN; v += 4) {
+        const float4 bb = *reinterpret_cast<const float4*>(tile + kk * kGLd + tx * TN + v);
+        bv[v] = bb.x; bv[v + 1] = bb.y; bv[v + 2] = bb.z; bv[v + 3] = bb.w;
+      }
+#pragma unroll
+      for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < TM; ++u)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const int r = ty * 4 + u, cc = tx * 8 + v;
+    for (int v = 0; v < TN; ++v) {
+      const int r = ty * TM + u, cc = tx * TN + v;
       if (r < b && cc < b) G[r + b * cc] = acc[u][v];
     }
   __syncthreads();
@@ -137,7 +149,8 @@ __host__ __device__ inline size_t batch_compress_smem(int dmax, int Rmax) {
          eig_smem_bytes(dmax, P, false);
 }
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, int Rmax, size_t smem_bytes) {
+template <int TH>
+__global__ void __launch_bounds__(TH) k_batch(BatchArgs a, int dmax, int Rmax, size_t smem_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_idx;
   __shared__ int s_rank[3];
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a, int dmax, 
         long long c = 1;
         for (int j = l + 1; j < 3; ++j) c *= d[j];
         const int P = R < d[l] ? R : d[l];
-        cta_gram(cur, (int)ah, d[l], (int)c, G, tile);
+        cta_gram<TH>(cur, (int)ah, d[l], (int)c, G, tile);
         EigArgs ea{};
         ea.G = G; ea.I = d[l]; ea.P = P; ea.U = U + offU; ea.sigma = gs + lay.sig + l * P0;
         ea.rank_out = &s_rank[l]; ea.mlsvd_tol = a.mlsvd_tol; ea.L = 3;
@@ -514,13 +527,19 @@ struct BatchPlan {
 // The CTA count follows from the shared-memory and thread budget of an SM
 // (analytically, so the workspace size does not depend on runtime state);
 // CTAs that cannot be resident at once simply start later and drain the queue.
-BatchPlan batch_plan(int B, int dmax, int Rmax, const cpd_options& o, size_t smem) {
-  BatchPlan p{};
+int batch_ctas(int TH, size_t smem, int B) {
   int per_sm = (int)((228 * 1024) / (smem + 1024));
-  if (per_sm > 2048 / kBatchThreads) per_sm = 2048 / kBatchThreads;
+  if (per_sm > 2048 / TH) per_sm = 2048 / TH;
+  if (per_sm > 32) per_sm = 32;
   if (per_sm < 1) per_sm = 1;
   const int sms = 152;
-  p.ctas = per_sm * sms < B ? per_sm * sms : B;
+  return per_sm * sms < B ? per_sm * sms : B;
+}
+
+BatchPlan batch_plan(int B, int dmax, int Rmax, const cpd_options& o, size_t smem) {
+  BatchPlan p{};
+  p.ctas = 0;                         // capacity: the most CTAs any candidate CTA size launches
+  for (int TH : kBatchThreadChoices) { const int c = batch_ctas(TH, smem, B); p.ctas = c > p.ctas ? c : p.ctas; }
   const BatchLayout lay = batch_layout(o.compress ? dmax : dmax, Rmax, o.maxiter);
   p.per_cta = lay.total;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -554,13 +573,75 @@ ExLayout batch_ex_layout(int B, int dmax, int Rmax, const cpd_options& o, size_t
   return e;
 }
 
-int launch_k_batch(const BatchArgs& a, int dmax, int Rmax, size_t smem, int ctas, cudaStream_t st) {
-  if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return CPD_ERR_CUDA;
-  if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return CPD_ERR_CUDA;
-  k_batch<<<ctas, kBatchThreads, smem, st>>>(a, dmax, Rmax, smem);
+template <int TH>
+cudaError_t launch_th(BatchArgs a, int dmax, int Rmax, size_t smem, cudaStream_t st) {
+  const int ctas = batch_ctas(TH, smem, a.B);
+  a.ctas = ctas;
+  cudaError_t e = cudaFuncSetAttribute(k_batch<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_batch<TH><<<ctas, TH, smem, st>>>(a, dmax, Rmax, smem);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+  return cudaGetLastError();
+}
+
+// Queue reset and one persistent launch with CTAs of TH threads.
+int launch_k_batch(const BatchArgs& a, int dmax, int Rmax, size_t smem, int TH, cudaStream_t st) {
+  if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return CPD_ERR_CUDA;
+  cudaError_t e = TH == 64 ? launch_th<64>(a, dmax, Rmax, smem, st)
+                           : TH == 256 ? launch_th<256>(a, dmax, Rmax, smem, st)
+                                       : launch_th<128>(a, dmax, Rmax, smem, st);
+  return e == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+}
+
+// Autotuner of the batched solver's CTA size (and with it the Gram tile shape
+// and the CTAs per SM): on the first call for a shape class (device, largest
+// mode, largest rank, compression, batch size rounded to a power of two) it
+// runs the whole batch once per candidate, timed with CUDA events on the
+// stream, and keeps the fastest for later calls.  Not while the stream is
+// being captured (the default, 128, is used then).  opts->block_threads of
+// 64, 128 or 256 fixes the choice.
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tuned;
+
+template <class Run>
+int batch_threads(const cpd_options& o, int dmax, int Rmax, int B, cudaStream_t st, Run run, int* rc) {
+  *rc = CPD_OK;
+  if (o.block_threads == 64 || o.block_threads == 128 || o.block_threads == 256) return o.block_threads;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int bb = 1;
+  while ((1 << bb) < B) ++bb;
+  const std::vector<long long> key = {dev, dmax, Rmax, o.compress, bb};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return 128;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { *rc = CPD_ERR_CUDA; return 128; }
+  int best = 128;
+  float best_ms = 3.4e38f;
+  for (int TH : kBatchThreadChoices) {
+    cudaEventRecord(e0, st);
+    const int r = run(TH);
+    cudaEventRecord(e1, st);
+    if (r != CPD_OK || cudaEventSynchronize(e1) != cudaSuccess) { *rc = r != CPD_OK ? r : CPD_ERR_CUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = TH; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (*rc == CPD_OK) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  return best;
 }
 
 std::vector<BatchItem> sorted_items(int B, const int64_t* t_off, const int* dims, const int* ranks,
@@ -578,6 +659,58 @@ std::vector<BatchItem> sorted_items(int B, const int64_t* t_off, const int* dims
     return cx > cy;
   });
   return items;
+}
+
+// Graphs of the plain batched solve, per argument set (pointers, options,
+// CTA size and a hash of the items), least recently used first out.  Each
+// keeps the pinned host copy of the sorted items its upload node reads.
+struct BatchGraphKey {
+  int dev, B, TH, pad;
+  unsigned long long h;
+  cpd_options o;
+  const float* T; float* W; float* lam; void* ws; size_t ws_bytes;
+};
+struct BatchGraphEntry { BatchGraphKey k; cudaGraphExec_t exec; BatchItem* pinned; unsigned long long used; };
+std::mutex g_bgraph_mu;
+std::vector<BatchGraphEntry> g_bgraphs;
+unsigned long long g_bgraph_clock = 0;
+constexpr size_t kMaxBatchGraphs = 8;
+
+unsigned long long fnv1a(unsigned long long h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+unsigned long long batch_hash(int B, const int64_t* t_off, const int* dims, const int* ranks, const int64_t* w_off,
+                              const int64_t* l_off) {
+  unsigned long long h = 1469598103934665603ull;
+  h = fnv1a(h, t_off, sizeof(int64_t) * B);
+  h = fnv1a(h, dims, sizeof(int) * 3 * B);
+  h = fnv1a(h, ranks, sizeof(int) * B);
+  h = fnv1a(h, w_off, sizeof(int64_t) * B);
+  h = fnv1a(h, l_off, sizeof(int64_t) * B);
+  return h;
+}
+
+cudaGraphExec_t batch_graph_get(const BatchGraphKey& k) {
+  std::lock_guard<std::mutex> lk(g_bgraph_mu);
+  for (auto& e : g_bgraphs)
+    if (memcmp(&e.k, &k, sizeof(k)) == 0) { e.used = ++g_bgraph_clock; return e.exec; }
+  return nullptr;
+}
+
+void batch_graph_put(const BatchGraphKey& k, cudaGraphExec_t exec, BatchItem* pinned) {
+  std::lock_guard<std::mutex> lk(g_bgraph_mu);
+  if (g_bgraphs.size() >= kMaxBatchGraphs) {
+    size_t victim = 0;
+    for (size_t i = 1; i < g_bgraphs.size(); ++i)
+      if (g_bgraphs[i].used < g_bgraphs[victim].used) victim = i;
+    cudaGraphExecDestroy(g_bgraphs[victim].exec);
+    cudaFreeHost(g_bgraphs[victim].pinned);
+    g_bgraphs.erase(g_bgraphs.begin() + victim);
+  }
+  g_bgraphs.push_back(BatchGraphEntry{k, exec, pinned, ++g_bgraph_clock});
 }
 
 // mode 0: plain method + network inputs and training targets; mode 1: learned start.
@@ -617,24 +750,29 @@ int batch_ex(int mode, int B, const float* T_packed, const int64_t* t_off, const
   a.store_floats = e.store_floats;
   float* Xw = (mode == 1 || X == nullptr) ? reinterpret_cast<float*>(ws + e.X) : X;
   float* Yw = reinterpret_cast<float*>(ws + e.Y);
-  {
-    ProfScope ps(st, "batch_compress");
-    a.phase = 1; a.X = Xw; a.init = CPD_INIT_MLSVD;
-    if ((v = launch_k_batch(a, dmax, Rmax, smem, e.p.ctas, st)) != CPD_OK) return v;
-  }
-  if (mode == 1) {
-    ProfScope ps(st, "initnet_forward");
-    if (initnet_forward(params, Xw, B, ws + e.act, Yw, st) != cudaSuccess) return CPD_ERR_CUDA;
-  }
-  {
+  auto run = [&](int TH) -> int {
+    int r;
+    {
+      ProfScope ps(st, "batch_compress");
+      a.phase = 1; a.X = Xw; a.init = CPD_INIT_MLSVD; a.Y = nullptr; a.target = nullptr; a.tmask = nullptr;
+      if ((r = launch_k_batch(a, dmax, Rmax, smem, TH, st)) != CPD_OK) return r;
+    }
+    if (mode == 1) {
+      ProfScope ps(st, "initnet_forward");
+      if (initnet_forward(params, Xw, B, ws + e.act, Yw, st) != cudaSuccess) return CPD_ERR_CUDA;
+    }
     ProfScope ps(st, "batch_solve");
     a.phase = 2; a.X = nullptr;
     a.init = mode == 1 ? CPD_INIT_LEARNED : CPD_INIT_MLSVD;
     a.Y = mode == 1 ? Yw : nullptr;
     a.target = mode == 0 ? target : nullptr;
     a.tmask = mode == 0 ? tmask : nullptr;
-    if ((v = launch_k_batch(a, dmax, Rmax, smem, e.p.ctas, st)) != CPD_OK) return v;
-  }
+    return launch_k_batch(a, dmax, Rmax, smem, TH, st);
+  };
+  int trc = CPD_OK;
+  const int TH = batch_threads(o, dmax, Rmax, B, st, run, &trc);
+  if (trc != CPD_OK) return trc;
+  if ((v = run(TH)) != CPD_OK) return v;
   if (infos) {
     if (cudaMemcpyAsync(infos, ws + e.p.infos, sizeof(cpd_info) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -672,23 +810,9 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
   const BatchPlan p = batch_plan(B, dmax, Rmax, o, smem);
   if (ws_bytes < p.total) return CPD_ERR_WORKSPACE;
   // items, longest first (cost ~ entries x mode sizes)
-  std::vector<BatchItem> items((size_t)B);
-  for (int b = 0; b < B; ++b) {
-    BatchItem& it = items[(size_t)b];
-    it.t_off = t_off[b]; it.w_off = w_off[b]; it.l_off = l_off[b];
-    it.d[0] = dims[3 * b]; it.d[1] = dims[3 * b + 1]; it.d[2] = dims[3 * b + 2];
-    it.R = ranks[b]; it.b = b; it.pad = 0;
-  }
-  std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
-    const double cx = (double)x.d[0] * x.d[1] * x.d[2] * (x.d[0] + x.d[1] + x.d[2]) + 4e3 * x.R * x.R;
-    const double cy = (double)y.d[0] * y.d[1] * y.d[2] * (y.d[0] + y.d[1] + y.d[2]) + 4e3 * y.R * y.R;
-    return cx > cy;
-  });
+  const std::vector<BatchItem> items = sorted_items(B, t_off, dims, ranks, w_off, l_off);
   char* ws = static_cast<char*>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(ws + p.items, items.data(), sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return CPD_ERR_CUDA;
-  if (cudaMemsetAsync(ws + p.queue, 0, 256, st) != cudaSuccess) return CPD_ERR_CUDA;
   BatchArgs a{};
   a.T = T_packed; a.W = W_packed; a.lam = lam_packed;
   a.items = reinterpret_cast<const BatchItem*>(ws + p.items);
@@ -700,13 +824,62 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
   a.hist = reinterpret_cast<double*>(ws + p.hist);
   a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
   a.mlsvd_tol = o.mlsvd_tol; a.compress = o.compress; a.init = o.init; a.seed = o.seed; a.ctas = p.ctas;
-  {
-    ProfScope ps(st, "batch");
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  auto direct = [&](int TH) -> int {
+    if (cudaMemcpyAsync(ws + p.items, items.data(), sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return CPD_ERR_CUDA;
-    k_batch<<<p.ctas, kBatchThreads, smem, st>>>(a, dmax, Rmax, smem);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return CPD_ERR_CUDA;
+    ProfScope ps(st, "batch");
+    return launch_k_batch(a, dmax, Rmax, smem, TH, st);
+  };
+  int trc = CPD_OK;
+  const int TH = batch_threads(o, dmax, Rmax, B, st, direct, &trc);
+  if (trc != CPD_OK) return trc;
+  // replay a captured graph (item upload from a pinned copy, queue reset, the
+  // persistent launch) when the stream allows it; graphs are cached per
+  // argument set
+  bool launched = false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (st != nullptr && !profile_enabled() && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
+    BatchGraphKey k;
+    memset(&k, 0, sizeof(k));
+    cudaGetDevice(&k.dev);
+    k.B = B; k.TH = TH; k.o = o; k.T = T_packed; k.W = W_packed; k.lam = lam_packed;
+    k.ws = workspace; k.ws_bytes = ws_bytes;
+    k.h = batch_hash(B, t_off, dims, ranks, w_off, l_off);
+    cudaGraphExec_t exec = batch_graph_get(k);
+    if (exec == nullptr) {
+      BatchItem* pinned = nullptr;
+      if (cudaMallocHost(reinterpret_cast<void**>(&pinned), sizeof(BatchItem) * B) == cudaSuccess) {
+        memcpy(pinned, items.data(), sizeof(BatchItem) * B);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          int rc = CPD_OK;
+          if (cudaMemcpyAsync(ws + p.items, pinned, sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = CPD_ERR_CUDA;
+          if (rc == CPD_OK) rc = launch_k_batch(a, dmax, Rmax, smem, TH, st);
+          count_launch(-1);                  // captured, not launched: counted when replayed
+          const cudaError_t ec = cudaStreamEndCapture(st, &g);
+          if (rc == CPD_OK && ec == cudaSuccess && g != nullptr && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+            batch_graph_put(k, exec, pinned);
+            pinned = nullptr;
+          } else {
+            exec = nullptr;
+          }
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+        }
+        if (pinned) cudaFreeHost(pinned);
+      }
+    }
+    if (exec != nullptr) {
+      if (cudaGraphLaunch(exec, st) != cudaSuccess) return CPD_ERR_CUDA;
+      count_launch(1);
+      launched = true;
+    }
+  }
+  if (!launched) {
+    const int rc = direct(TH);
+    if (rc != CPD_OK) return rc;
   }
   if (infos) {
     if (cudaMemcpyAsync(infos, ws + p.infos, sizeof(cpd_info) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -144,3 +144,32 @@ def test_batch_full_4096_sampled_parity(cpd):
     pick = np.random.default_rng(123).choice(len(items), size=32, replace=False)
     out = [check_item(items[int(b)], *res[int(b)], int(b), 1e-6) for b in pick]
     summarize(out, 0.75, 0.85)
+
+
+def test_batch_graph_replay_and_cta_sizes(cpd):
+    """On a non-default stream the batch is captured once into a CUDA graph and
+    replayed: repeated calls give identical results.  Every CTA size the
+    autotuner chooses between (64, 128, 256 threads, with their Gram tiles)
+    solves the items to the same fits."""
+    items = synth.c4_batch(seed=10, B=64, lo=6, hi=30, rlo=1, rhi=6, eta=1e-6)
+    Tp, offs = pack(items)
+    dims = [list(it["T"].shape) for it in items]
+    ranks = [it["R"] for it in items]
+    st = torch.cuda.Stream()
+    outs = []
+    for _ in range(3):
+        with torch.cuda.stream(st):
+            W, lam, w_off, l_off, infos = cpd.cpd_batch_solve(Tp, offs, dims, ranks, cpd.cpd_default_options(seed=5),
+                                                              stream=st)
+        torch.cuda.synchronize()
+        outs.append((W.clone(), lam.clone()))
+    assert all(torch.equal(outs[0][0], o[0]) and torch.equal(outs[0][1], o[1]) for o in outs[1:])
+    fits = {}
+    for th in (64, 128, 256):
+        res, inf = run_batch(cpd, items, seed=5, block_threads=th)
+        assert all(i["status"] == 0 for i in inf)
+        fits[th] = [O.fit(it["T"].astype(np.float64), *res[b]) for b, it in enumerate(items)]
+    for b in range(len(items)):
+        f = [fits[th][b] for th in (64, 128, 256)]
+        if min(f) < 1e-5:
+            assert max(f) - min(f) <= 5e-6, f
