@@ -238,12 +238,33 @@ static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, doubl
   }
 }
 
+// Q[:, j] for one row i from L q^T = z^T (forward substitution), with the
+// unknowns of the row in registers: MB bounds m at compile time so that the
+// loops unroll (a runtime-sized array would live in local memory).
+template <int MB>
+static __device__ void fwd_subst(const float* Z, float* Q, int I, int m, const float* Lf) {
+  for (int i = threadIdx.x; i < I; i += blockDim.x) {
+    float q[MB];
+#pragma unroll
+    for (int j = 0; j < MB; ++j) {
+      if (j < m) {
+        float t = Z[j * I + i];
+#pragma unroll
+        for (int k = 0; k < j; ++k) t = fmaf(-Lf[j * m + k], q[k], t);
+        q[j] = t / Lf[j * m + j];
+        Q[j * I + i] = q[j];
+      }
+    }
+  }
+}
+
 // Z (I x m, column-major, ld I) -> orthonormal Q with span(Q) = span(Z) by
 // Cholesky QR on column-normalised Z (FP32; C = Z^T Z has unit diagonal, and
 // a pivot below 1e-5 marks a column as dependent on the previous ones).
 // Dependent columns are replaced by pseudo-random +-1 vectors and the
 // factorisation is repeated.  Warp-parallel dots; Cholesky by warp 0;
 // row-wise forward substitution.  Returns false if it did not succeed.
+template <int MMAX>
 static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float* Cf, uint64_t seed, int salt) {
   __shared__ int bad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -307,15 +328,10 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
       continue;
     }
     // Q = Z L^{-T}: row-wise forward substitution L q^T = z^T
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-      float q[kMaxM];
-      for (int j = 0; j < m; ++j) {
-        float t = Z[j * I + i];
-        for (int k = 0; k < j; ++k) t = fmaf(-Lf[j * m + k], q[k], t);
-        q[j] = t / Lf[j * m + j];
-      }
-      for (int j = 0; j < m; ++j) Q[j * I + i] = q[j];
-    }
+    if (m <= 16) fwd_subst<16>(Z, Q, I, m, Lf);
+    else if constexpr (MMAX <= 32) fwd_subst<32>(Z, Q, I, m, Lf);
+    else if (m <= 32) fwd_subst<32>(Z, Q, I, m, Lf);
+    else fwd_subst<kMaxM>(Z, Q, I, m, Lf);
     __syncthreads();
     return true;
   }
@@ -388,6 +404,9 @@ __host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g) {
 // by the whole CTA, with `smem_raw` as shared-memory workspace of
 // eig_smem_bytes(I, P, g_in_smem) bytes.  a.work == nullptr means: copy G into
 // that workspace first (it fits); otherwise G is read where it is.
+// MMAX: the largest subspace width the caller needs (72 for the eigen
+// kernel, 32 for the batched solver's modes of at most 64).
+template <int MMAX = kMaxM>
 static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
   const int I = a.I, P = a.P, m = eig_m(I, P);
   // layout: red(128 d) | H, V, W1, W2 (m*m d each) | Lf(m*m) | Cf(m) | Q(I*m) | Z(I*m) | G(I*I if it fits)
@@ -429,10 +448,10 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     gram_times(G, Q, Z, I, m);
     double prev = -1.0;
     for (int it = 0; it < 30; ++it) {
-      cholqr(Z, Q, I, m, Lf, Cf, a.seed, it);
+      cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, it);
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) Z[e] = Q[e];
       __syncthreads();
-      cholqr(Z, Q, I, m, Lf, Cf, a.seed, 1000 + it);
+      cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, 1000 + it);
       gram_times(G, Q, Z, I, m);
       float vf[1] = {0.f};
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) vf[0] = fmaf(Q[e], Z[e], vf[0]);

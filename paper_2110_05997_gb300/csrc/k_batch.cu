@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(TH) k_batch(BatchArgs a, int dmax, int Rmax, s
         ea.rank_out = &s_rank[l]; ea.mlsvd_tol = a.mlsvd_tol; ea.L = 3;
         ea.seed = seed + 7919ull * (uint64_t)l;
         ea.work = G;                                   // non-null: G is read in place
-        eig_run(ea, eigw);
+        eig_run<32>(ea, eigw);
         __syncthreads();
         const int rk = s_rank[l];
         for (int e = threadIdx.x; e < d[l] * rk; e += blockDim.x) Us[e] = U[offU + e];
