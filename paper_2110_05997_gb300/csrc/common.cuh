@@ -79,6 +79,32 @@ __device__ inline void block_sum(const float (&in)[NV], double (&out)[NV], doubl
   }
 }
 
+// As block_sum, the totals left in FP32 (no FP64 conversion in every warp).
+template <int NV>
+__device__ inline void block_sum_f(const float (&in)[NV], float (&out)[NV], double* red) {
+  float v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    v[i] = in[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float* r = reinterpret_cast<float*>(red);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) r[i * 32 + wid] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float s = lane < nw ? r[i * 32 + lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    out[i] = s;
+  }
+}
+
 // a / b and sqrt(x) to ~FP64 accuracy from an FP32 estimate and one FP64
 // correction step (2-3 FP64 FMAs instead of a full FP64 division / square
 // root sequence).  Valid while a, b, x are within the FP32 exponent range.

@@ -168,6 +168,11 @@ __device__ __forceinline__ float hv_entry(const Shape& s, const Bufs& b, const f
 // ||r||^2 < tol or maxit; x_hat is left in b.X.  Returns the iterations run.
 template <int L>
 __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  // The inner products are FP32 block sums; alpha and beta are FP32 quotients
+  // of them (the updates use FP32 alpha and beta, and the correctly rounded
+  // FP32 quotient is what an FP64 quotient rounded to FP32 gives, barring
+  // double rounding), so no warp repeats FP64 scalar work; the stop test
+  // compares ||r||^2 with tol in FP64.
   const int n = s.n, R = s.R;
   float v[1] = {0.f};
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -177,9 +182,9 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
     b.Rr[j] = rv; b.P[j] = rv; b.X[j] = 0.f; b.Tmp[j] = m * rv;
     v[0] = fmaf(rv, rv, v[0]);
   }
-  double rr0[1];
-  block_sum<1>(v, rr0, b.red);
-  double rr = rr0[0];
+  float rr0[1];
+  block_sum_f<1>(v, rr0, b.red);
+  float rr = rr0[0];
   int its = 0;
   for (int it = 0; it < maxit; ++it) {
     hv_xy<L>(s, b, b.Tmp);
@@ -192,31 +197,30 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
       b.Z[j] = z;
       pzf[0] = fmaf(b.P[j], z, pzf[0]);
     }
-    double pz[1];
-    block_sum<1>(pzf, pz, b.red);
-    if (!(pz[0] > 0.0)) break;
-    const double alpha = warp_div(rr, pz[0]);
+    float pz[1];
+    block_sum_f<1>(pzf, pz, b.red);
+    if (!(pz[0] > 0.f)) break;
+    const float af = rr / pz[0];
     float rnf[1] = {0.f};
-    const float af = (float)alpha;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       b.X[j] = fmaf(af, b.P[j], b.X[j]);
       const float rv = fmaf(-af, b.Z[j], b.Rr[j]);
       b.Rr[j] = rv;
       rnf[0] = fmaf(rv, rv, rnf[0]);
     }
-    double rn[1];
-    block_sum<1>(rnf, rn, b.red);
-    const double beta = rr > 0.0 ? warp_div(rn[0], rr) : 0.0;
+    float rn[1];
+    block_sum_f<1>(rnf, rn, b.red);
+    const float bf = rr > 0.f ? rn[0] / rr : 0.f;
     rr = rn[0];
     its = it + 1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       int l, i, r; decode_j<L>(s, j, l, i, r);
-      const float pv = fmaf((float)beta, b.P[j], b.Rr[j]);
+      const float pv = fmaf(bf, b.P[j], b.Rr[j]);
       b.P[j] = pv;
       b.Tmp[j] = b.msq[l * R + r] * pv;
     }
     __syncthreads();
-    if (rr < tol) break;
+    if ((double)rr < tol) break;
   }
   return its;
 }
@@ -224,7 +228,8 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
 // The same PCG when every thread owns at most one unknown (n <= blockDim.x):
 // x, r, p, the preconditioner entry and the decoded index stay in registers
 // and only M^{-1/2} p (the vector J^T J is applied to) goes through shared
-// memory.  Same operations in the same order as pcg(), so the same results.
+// memory.  Same operations in the same order as pcg(), so the same results
+// (FP32 scalars as described there).
 template <int L>
 __device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
   const int n = s.n, R = s.R;
@@ -243,9 +248,9 @@ __device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, do
     b.Tmp[j] = m * rj;
     v[0] = rj * rj;
   }
-  double rr0[1];
-  block_sum<1>(v, rr0, b.red);
-  double rr = rr0[0];
+  float rr0[1];
+  block_sum_f<1>(v, rr0, b.red);
+  float rr = rr0[0];
   int its = 0;
   for (int it = 0; it < maxit; ++it) {
     hv_xy<L>(s, b, b.Tmp);
@@ -255,28 +260,27 @@ __device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, do
       z = m * (hv_entry<L>(s, b, b.Tmp, l, i, r) + mg * (m * pj));
       pzf[0] = pj * z;
     }
-    double pz[1];
-    block_sum<1>(pzf, pz, b.red);
-    if (!(pz[0] > 0.0)) break;
-    const double alpha = warp_div(rr, pz[0]);
-    const float af = (float)alpha;
+    float pz[1];
+    block_sum_f<1>(pzf, pz, b.red);
+    if (!(pz[0] > 0.f)) break;
+    const float af = rr / pz[0];
     float rnf[1] = {0.f};
     if (own) {
       x = fmaf(af, pj, x);
       rj = fmaf(-af, z, rj);
       rnf[0] = rj * rj;
     }
-    double rn[1];
-    block_sum<1>(rnf, rn, b.red);
-    const double beta = rr > 0.0 ? warp_div(rn[0], rr) : 0.0;
+    float rn[1];
+    block_sum_f<1>(rnf, rn, b.red);
+    const float bf = rr > 0.f ? rn[0] / rr : 0.f;
     rr = rn[0];
     its = it + 1;
     if (own) {
-      pj = fmaf((float)beta, pj, rj);
+      pj = fmaf(bf, pj, rj);
       b.Tmp[j] = m * pj;
     }
     __syncthreads();
-    if (rr < tol) break;
+    if ((double)rr < tol) break;
   }
   if (own) b.X[j] = x;
   __syncthreads();
