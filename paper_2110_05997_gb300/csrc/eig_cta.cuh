@@ -258,11 +258,71 @@ static __device__ void fwd_subst(const float* Z, float* Q, int I, int m, const f
   }
 }
 
+// Right-looking Cholesky of the symmetric m x m matrix in Lf (m <= MB <= 32)
+// by one warp: lane i keeps row i of the running Schur complement in
+// registers; step j broadcasts the pivot and the scaled column j by shuffles
+// and updates every later entry of the row.  On exit the lower triangle of Lf
+// holds L; `bad` gets the first column whose pivot is not above 1e-5 (the
+// factor is then incomplete and not written).
+template <int MB>
+static __device__ void chol_warp(float* Lf, int m, int lane, int& bad) {
+  float row[MB];
+#pragma unroll
+  for (int k = 0; k < MB; ++k) row[k] = (lane < m && k < m) ? Lf[lane * m + k] : 0.f;
+  int fail = -1;
+#pragma unroll
+  for (int j = 0; j < MB; ++j) {
+    if (j < m && fail < 0) {
+      const float piv = __shfl_sync(0xffffffffu, row[j], j);
+      if (!(piv > 1e-5f)) {
+        fail = j;
+      } else {
+        const float ljj = sqrtf(piv);
+        const float lij = lane > j ? row[j] / ljj : (lane == j ? ljj : 0.f);
+        row[j] = lij;
+#pragma unroll
+        for (int k = j + 1; k < MB; ++k) row[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), row[k]);
+      }
+    }
+  }
+  if (fail >= 0) {
+    if (lane == 0) bad = fail;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < MB; ++k)
+    if (k <= lane && lane < m) Lf[lane * m + k] = row[k];
+}
+
+// Left-looking Cholesky by one warp for m > 32 (same contract as chol_warp).
+static __device__ void chol_warp_left(float* Lf, int m, int lane, int& bad) {
+  for (int j = 0; j < m; ++j) {
+    float s = 0.f;
+    for (int k = lane; k < j; k += 32) s = fmaf(Lf[j * m + k], Lf[j * m + k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float piv = Lf[j * m + j] - s;
+    __syncwarp();
+    if (!(piv > 1e-5f)) { if (lane == 0) bad = j; return; }
+    const float ljj = sqrtf(piv);
+    const float inv = 1.f / ljj;
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      float t = Lf[i * m + j];
+      for (int k = 0; k < j; ++k) t = fmaf(-Lf[i * m + k], Lf[j * m + k], t);
+      Lf[i * m + j] = t * inv;
+    }
+    __syncwarp();
+    if (lane == 0) Lf[j * m + j] = ljj;
+    __syncwarp();
+  }
+}
+
 // Z (I x m, column-major, ld I) -> orthonormal Q with span(Q) = span(Z) by
 // Cholesky QR on column-normalised Z (FP32; C = Z^T Z has unit diagonal, and
 // a pivot below 1e-5 marks a column as dependent on the previous ones).
 // Dependent columns are replaced by pseudo-random +-1 vectors and the
-// factorisation is repeated.  Warp-parallel dots; Cholesky by warp 0;
+// factorisation is repeated.  Warp-parallel dots; Cholesky by warp 0
+// (right-looking in registers up to m = 32);
 // row-wise forward substitution.  Returns false if it did not succeed.
 template <int MMAX>
 static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float* Cf, uint64_t seed, int salt) {
@@ -279,41 +339,42 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
     __syncthreads();
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) Z[e] *= Cf[e / I];
     __syncthreads();
-    // C = Z^T Z: one warp per upper-triangle entry
+    // C = Z^T Z: one thread per upper-triangle entry (r, c), four partial
+    // sums.  For even I the thread starts its pass over the rows at row c
+    // (cyclically), so that a warp's 32 consecutive columns c fall in
+    // distinct banks; for odd I the column stride already does.
     const int ntri = m * (m + 1) / 2;
-    for (int t = warp; t < ntri; t += nwarp) {
+    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
       int r = 0, rem = t;
       while (rem >= m - r) { rem -= m - r; ++r; }
       const int c = r + rem;
-      float s = 0.f;
-      for (int i = lane; i < I; i += 32) s = fmaf(Z[r * I + i], Z[c * I + i], s);
+      const float* zr = Z + r * I;
+      const float* zc = Z + c * I;
+      int i = (I & 1) ? 0 : c % I;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      int q = 0;
+      for (; q + 4 <= I; q += 4) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) { Lf[r * m + c] = s; Lf[c * m + r] = s; }
+        for (int u = 0; u < 4; ++u) {
+          acc[u] = fmaf(zr[i], zc[i], acc[u]);
+          if (++i == I) i = 0;
+        }
+      }
+      for (; q < I; ++q) {
+        acc[0] = fmaf(zr[i], zc[i], acc[0]);
+        if (++i == I) i = 0;
+      }
+      const float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      Lf[r * m + c] = s;
+      Lf[c * m + r] = s;
     }
     if (threadIdx.x == 0) bad = -1;
     __syncthreads();
     // Cholesky C = L L^T by warp 0, L in the lower triangle of Lf
     if (warp == 0) {
-      for (int j = 0; j < m; ++j) {
-        float s = 0.f;
-        for (int k = lane; k < j; k += 32) s = fmaf(Lf[j * m + k], Lf[j * m + k], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const float piv = Lf[j * m + j] - s;
-        __syncwarp();
-        if (!(piv > 1e-5f)) { if (lane == 0) bad = j; break; }
-        const float ljj = sqrtf(piv);
-        const float inv = 1.f / ljj;
-        for (int i = j + 1 + lane; i < m; i += 32) {
-          float t = Lf[i * m + j];
-          for (int k = 0; k < j; ++k) t = fmaf(-Lf[i * m + k], Lf[j * m + k], t);
-          Lf[i * m + j] = t * inv;
-        }
-        __syncwarp();
-        if (lane == 0) Lf[j * m + j] = ljj;
-        __syncwarp();
-      }
+      if (m <= 16) chol_warp<16>(Lf, m, lane, bad);
+      else if (m <= 32) chol_warp<32>(Lf, m, lane, bad);
+      else chol_warp_left(Lf, m, lane, bad);
     }
     __syncthreads();
     if (bad >= 0) {
