@@ -114,6 +114,7 @@ def workload():
 STAGE_SOURCES = {
     "dgn_core": ["k_dgn.cu", "dgn_cta.cuh", "solver.cuh", "common.cuh", "kernels.h"],
     "gram_bf16_tc": ["k_gram_tc.cu", "kernels.h"],
+    "refine_pass": ["k_refine_pass3.cu", "refine_pass.cuh", "solver.cuh", "common.cuh", "kernels.h"],
 }
 
 
