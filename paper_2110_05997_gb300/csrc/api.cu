@@ -250,8 +250,13 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
 }
 
 // The launch sequence of one solve (Fig. "tensorfox-flow"), enqueued on st.
+// `side` (optional) is an idle stream on which, while st is being captured,
+// the refinement iterations are captured as the body of a conditional while
+// node (*refine_loop = 1); otherwise all refine_maxiter + 1 iterations are
+// enqueued and the stopped ones exit at once.
 int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, int L, int R,
-                  const float* W0, float* W_out, float* lambda_out, double* trace, cudaStream_t st) {
+                  const float* W0, float* W_out, float* lambda_out, double* trace, cudaStream_t st,
+                  cudaStream_t side = nullptr, int* refine_loop = nullptr) {
   const int trace_cap = trace ? (o.maxiter + o.refine_maxiter) : 0;
 
   // ---- compression and initial factors -----------------------------------------
@@ -308,11 +313,47 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
     sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
     sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
     const int rthreads = 1024;
-    for (int j = 0; j <= o.refine_maxiter; ++j) {
-      pa.want_tsq = (j == 0);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (side != nullptr && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
+      // iteration 0, then a while node whose body is one iteration; every
+      // exit of the step kernel sets the condition, so the graph runs only
+      // the iterations the stop tests allow (at most refine_maxiter)
+      cudaGraph_t g = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* ed = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+      cudaGraphConditionalHandle h;
+      CK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+      sa.use_cond = 1; sa.cond = h;
+      pa.want_tsq = 1; sa.j = 0;
       PL("refine_pass", launch_refine_pass(pa, st));
-      sa.j = j;
       PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+      CK(cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      pa.want_tsq = 0; sa.j_from_state = 1;
+      cudaError_t e = launch_refine_pass(pa, side);
+      if (e == cudaSuccess) e = launch_refine_step(sa, rthreads, p.r_smem, side);
+      cudaGraph_t body = nullptr;                 // owned by the conditional node
+      const cudaError_t ee = cudaStreamEndCapture(side, &body);
+      CK(e);
+      CK(ee);
+      CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      if (refine_loop) *refine_loop = 1;
+    } else {
+      for (int j = 0; j <= o.refine_maxiter; ++j) {
+        pa.want_tsq = (j == 0);
+        PL("refine_pass", launch_refine_pass(pa, st));
+        sa.j = j;
+        PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+      }
     }
     Wfinal = Wr;
   }
@@ -331,13 +372,26 @@ struct GraphKey {
   cpd_options o;
   const void* T; const float* W0; float* W_out; float* lam; double* trace; void* ws; size_t ws_bytes;
 };
-struct GraphEntry { GraphKey k; cudaGraphExec_t exec; unsigned long long used; long long kernels; };
+struct GraphEntry { GraphKey k; cudaGraphExec_t exec; unsigned long long used; long long kernels; int refine_loop; };
 std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;
 unsigned long long g_graph_clock = 0;
 constexpr size_t kMaxGraphs = 16;
 
 bool same_key(const GraphKey& a, const GraphKey& b) { return memcmp(&a, &b, sizeof(GraphKey)) == 0; }
+
+// An idle stream per thread and device for capturing graph-loop bodies
+// (created before any capture begins).
+cudaStream_t side_stream() {
+  static thread_local cudaStream_t s[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (s[dev] == nullptr && cudaStreamCreateWithFlags(&s[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    s[dev] = nullptr;
+    cudaGetLastError();
+  }
+  return s[dev];
+}
 
 }  // namespace
 
@@ -414,6 +468,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   cudaStream_t st = as_stream(stream);
   // replay a captured graph of the launch sequence when the stream allows it
   bool launched = false;
+  int refine_loop = 0;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (st != nullptr && !profile_enabled() && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
       cap == cudaStreamCaptureStatusNone) {
@@ -426,16 +481,21 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     k.ws = workspace; k.ws_bytes = ws_bytes;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
+    int loop = 0;
     {
       std::lock_guard<std::mutex> lk(g_graph_mu);
       for (auto& e : g_graphs)
-        if (same_key(e.k, k)) { exec = e.exec; kernels = e.kernels; e.used = ++g_graph_clock; break; }
+        if (same_key(e.k, k)) {
+          exec = e.exec; kernels = e.kernels; loop = e.refine_loop; e.used = ++g_graph_clock;
+          break;
+        }
     }
     if (exec == nullptr) {
       cudaGraph_t g = nullptr;
+      cudaStream_t side = o.refine_maxiter > 0 ? side_stream() : nullptr;
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         const long long before = cpd_launch_count();
-        const int rc = enqueue_solve(p, o, T, dtype, L, R, W0, W_out, lambda_out, trace, st);
+        const int rc = enqueue_solve(p, o, T, dtype, L, R, W0, W_out, lambda_out, trace, st, side, &loop);
         kernels = cpd_launch_count() - before;
         count_launch(-(int)kernels);     // captured, not launched: counted when replayed
         const cudaError_t ec = cudaStreamEndCapture(st, &g);
@@ -449,9 +509,10 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
             cudaGraphExecDestroy(g_graphs[victim].exec);
             g_graphs.erase(g_graphs.begin() + victim);
           }
-          g_graphs.push_back(GraphEntry{k, exec, ++g_graph_clock, kernels});
+          g_graphs.push_back(GraphEntry{k, exec, ++g_graph_clock, kernels, loop});
         } else {
           exec = nullptr;
+          loop = 0;
         }
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();          // a failed capture falls back to direct launches
@@ -459,8 +520,9 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     }
     if (exec != nullptr) {
       if (cudaGraphLaunch(exec, st) != cudaSuccess) return CPD_ERR_CUDA;
-      count_launch((int)kernels);      // the kernels the graph replays
+      count_launch((int)kernels);      // the kernels the graph replays (a loop body once)
       launched = true;
+      refine_loop = loop;
     }
   }
   if (!launched) {
@@ -473,10 +535,13 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     CK(cudaMemcpyAsync(&hr, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
     int core_dims[CPD_MAX_ORDER] = {0, 0, 0, 0};
     if (o.compress) CK(cudaMemcpyAsync(core_dims, p.core_dims_dev, sizeof(int) * CPD_MAX_ORDER, cudaMemcpyDeviceToHost, st));
-    int r_iters = 0, r_stop = 0, r_cg = 0, r_status = CPD_OK; double r_err = 0.0, r_mu = 0.0;
+    int r_iters = 0, r_stop = 0, r_cg = 0, r_status = CPD_OK, r_steps = 0; double r_err = 0.0, r_mu = 0.0;
     if (o.refine_maxiter > 0)
-      CK(read_refine_result(p.rstate, &r_iters, &r_stop, &r_cg, &r_err, &r_mu, &r_status, st));
+      CK(read_refine_result(p.rstate, &r_iters, &r_stop, &r_cg, &r_err, &r_mu, &r_status, &r_steps, st));
     CK(cudaStreamSynchronize(st));
+    // a replayed loop body ran max(0, steps - 1) times (the first step is
+    // before the loop): correct the launch count by its 3 kernels a run
+    if (refine_loop) count_launch(3 * ((r_steps > 1 ? r_steps - 1 : 0) - 1));
     memset(info, 0, sizeof(*info));
     info->status = hr.status;
     info->iters = hr.iters;

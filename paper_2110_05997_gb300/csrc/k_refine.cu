@@ -11,7 +11,7 @@ namespace cpdk {
 
 struct RefineState {
   double mu, F, normT, pred_drop, step;
-  int kglob, cg_total, stop, status, iters, pad;
+  int kglob, cg_total, stop, status, iters, jnext;   // jnext: steps that got past the stop flag
   double rel_err;
 };
 
@@ -63,18 +63,28 @@ size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_sm
   return 128 * sizeof(double) + f * sizeof(float);
 }
 
+// In a graph loop (use_cond) every exit sets the loop condition: 0 once the
+// refinement has stopped or j = maxiter, else 1; j comes from the state's
+// counter, so the body's launch arguments are the same in every iteration.
 template <int L>
 __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
-  if (*a.done) return;
+  if (*a.done) {
+    if (a.use_cond && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_j;
   __shared__ Shape s;
   if (threadIdx.x == 0) {
     int dims[kMaxL];
     for (int l = 0; l < kMaxL; ++l) dims[l] = (l < L) ? (int)a.dims[l] : 1;
     make_shape(s, L, dims, a.R);
+    const int jj = a.j_from_state ? a.state->jnext : a.j;
+    a.state->jnext = jj + 1;
+    s_j = jj;
   }
   __syncthreads();
+  const int jr = s_j;                          // this step's refinement iteration
   const int R = a.R;
   const size_t RR = (size_t)R * R;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
@@ -99,7 +109,10 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   if (threadIdx.x == 0) {
     s_stop = 0;
     const double esq = a.esq[0];
-    if (a.j == 0) {
+    if (jr > a.maxiter) {                       // not reached: the loop condition ends at maxiter
+      if (st->stop == CPD_STOP_NONE) st->stop = CPD_STOP_MAXITER;
+      s_stop = 1;
+    } else if (jr == 0) {
       st->normT = sqrt(a.esq[1]);
       st->F = 0.5 * esq;
       st->rel_err = st->normT > 0.0 ? sqrt(esq) / st->normT : 0.0;
@@ -110,14 +123,14 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
       const double Fn = 0.5 * esq;
       const double gain = gain_update(st->F, Fn, st->pred_drop, mu);
       const double e = st->normT > 0.0 ? quick_div(quick_sqrt(esq), st->normT) : 0.0;
-      st->mu = mu; st->F = Fn; st->rel_err = e; st->iters = a.j;
-      a.hist[a.j] = e;
-      write_trace(a.trace, a.trace_cap, a.trace_slot0 + a.j - 1, st->kglob, e, mu, gain,
+      st->mu = mu; st->F = Fn; st->rel_err = e; st->iters = jr;
+      a.hist[jr] = e;
+      write_trace(a.trace, a.trace_cap, a.trace_slot0 + jr - 1, st->kglob, e, mu, gain,
                   -1, st->step, ginf, 1);
       int stop;
       if (!isfinite(esq) || !isfinite(st->step)) { st->status = CPD_ERR_NUMERIC; stop = CPD_STOP_NONE; s_stop = 1; }
       else {
-        stop = stop_test(a.j, a.maxiter, a.tol, e, st->step, ginf,
+        stop = stop_test(jr, a.maxiter, a.tol, e, st->step, ginf,
                          divergence_threshold(st->normT, a.tol), a.hist);
         if (stop != CPD_STOP_NONE) { st->stop = stop; s_stop = 1; }
       }
@@ -125,7 +138,10 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
     if (s_stop) *a.done = 1;
   }
   __syncthreads();
-  if (s_stop) return;
+  if (s_stop) {
+    if (a.use_cond && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+    return;
+  }
   const double mu = st->mu;
   __shared__ int s_maxit;
   const int kglob = st->kglob + 1;
@@ -140,8 +156,9 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) a.W[j] = b.W[j];
   if (threadIdx.x == 0) {
     st->pred_drop = pred_drop; st->step = quick_sqrt(step); st->kglob = kglob; st->cg_total += its;
-    if (a.trace && a.trace_slot0 + a.j < a.trace_cap)
-      a.trace[(size_t)(a.trace_slot0 + a.j) * CPD_TRACE_FIELDS + 4] = its;
+    if (a.trace && a.trace_slot0 + jr < a.trace_cap)
+      a.trace[(size_t)(a.trace_slot0 + jr) * CPD_TRACE_FIELDS + 4] = its;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, jr + 1 <= a.maxiter ? 1u : 0u);
   }
 }
 
@@ -157,7 +174,7 @@ cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem
 
 __global__ void k_refine_init(RefineState* s, const DevResult* core, int* done) {
   s->mu = core->mu; s->F = 0.0; s->normT = 0.0; s->pred_drop = 0.0; s->step = 0.0;
-  s->kglob = core->kglob; s->cg_total = 0; s->stop = 0; s->status = CPD_OK; s->iters = 0;
+  s->kglob = core->kglob; s->cg_total = 0; s->stop = 0; s->status = CPD_OK; s->iters = 0; s->jnext = 0;
   s->rel_err = 0.0;
   *done = (core->status != CPD_OK) ? 1 : 0;
 }
@@ -169,7 +186,7 @@ cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, in
 }
 
 cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, int* cg_total,
-                               double* rel_err, double* mu, int* status, cudaStream_t st) {
+                               double* rel_err, double* mu, int* status, int* steps_run, cudaStream_t st) {
   static thread_local RefineState h;
   cudaError_t e = cudaMemcpyAsync(&h, state, sizeof(RefineState), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
@@ -177,6 +194,7 @@ cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, 
   if (e != cudaSuccess) return e;
   *iters = h.iters; *stop = h.stop; *cg_total = h.cg_total; *rel_err = h.rel_err; *mu = h.mu;
   *status = h.status;
+  if (steps_run) *steps_run = h.jnext;
   return cudaSuccess;
 }
 

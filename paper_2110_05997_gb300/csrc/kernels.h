@@ -170,6 +170,9 @@ struct RefineStepArgs {
   int* done;
   const int* cgtab;           // cg_maxiter(k) table written by the core solver
   int cgtab_len;
+  int j_from_state;           // 1: j is the state's iteration counter (a graph loop body)
+  int use_cond;               // 1: set `cond` to 1 when another iteration follows, else 0
+  cudaGraphConditionalHandle cond;
 };
 size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem);
 cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st);
@@ -177,7 +180,7 @@ cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, in
                                cudaStream_t st);
 size_t refine_state_bytes();
 cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, int* cg_total,
-                               double* rel_err, double* mu, int* status, cudaStream_t st);
+                               double* rel_err, double* mu, int* status, int* steps_run, cudaStream_t st);
 
 // ---- batched (k_batch.cu) ----------------------------------------------------------
 struct BatchItem {
