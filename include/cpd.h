@@ -161,6 +161,14 @@ int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_op
  *   info       host (synchronises the stream); may be NULL (no sync)
  *   trace      device, CPD_TRACE_FIELDS doubles per iteration, capacity
  *              (maxiter + refine_maxiter) records, or NULL
+ * Refinement (refine_maxiter > 0) needs I_1 <= 1024 for R <= 16, <= 512 for
+ * R <= 32, <= 256 for R <= 64, a product of I_2..I_L below 2^31, and its
+ * pass's shared memory (two copies of the factor blocks of modes 2..L plus
+ * I_1 x (33 + padded R) floats) within 227 KB; else CPD_ERR_UNSUPPORTED.
+ * On a non-default stream the launch sequence is captured once per argument
+ * set into a CUDA graph and replayed; its refinement iterations are the body
+ * of a conditional while node, so only the iterations the stop tests allow
+ * are launched.
  */
 int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
                   const cpd_options* opts, const float* W0, float* W_out, float* lambda_out,
@@ -342,6 +350,7 @@ int cpd_mode_gram(const float* T, int L, const int64_t* dims, int mode, int prec
  * cpd_refine_eval — one pass over a large tensor T (FP32): residual
  * e = T - [[W]], esq = ||e||^2 (FP64 accumulation, device double[1]) and the
  * MTTKRP of e for every mode into g_out (stacked blocks, = -grad F).
+ * Same shape limits as refinement in cpd_dgn_solve (else CPD_ERR_UNSUPPORTED).
  */
 int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const float* W,
                     float* g_out, double* esq_out, void* workspace, size_t ws_bytes,

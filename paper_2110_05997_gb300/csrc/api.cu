@@ -27,6 +27,12 @@ struct Carver {
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+bool pass_ok(int L, const int64_t* dims, int R) {
+  long long d[CPD_MAX_ORDER] = {1, 1, 1, 1};
+  for (int l = 0; l < L && l < CPD_MAX_ORDER; ++l) d[l] = dims[l];
+  return refine_pass_supported(L, d, R);
+}
+
 int validate_common(int L, const int64_t* dims, int R) {
   if (dims == nullptr) return CPD_ERR_INVALID_ARG;
   if (L < 1 || R < 1) return CPD_ERR_INVALID_ARG;
@@ -459,7 +465,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   if (o.gram_precision == CPD_GRAM_BF16 && !o.compress) return CPD_ERR_INVALID_ARG;
   if (o.gram_precision == CPD_GRAM_BF16 && !gram_bf16_tc_supported(dims[0], static_cast<const float*>(T)))
     return CPD_ERR_UNSUPPORTED;
-  if (o.refine_maxiter > 0 && !refine_pass_supported((int)dims[0], R)) return CPD_ERR_UNSUPPORTED;
+  if (o.refine_maxiter > 0 && !pass_ok(L, dims, R)) return CPD_ERR_UNSUPPORTED;
 
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
   Carver c(workspace, ws_bytes);
@@ -665,7 +671,7 @@ int cpd_refine_eval(const float* T, int L, const int64_t* dims, int R, const flo
   int v = validate_common(L, dims, R);
   if (v != CPD_OK) return v;
   if (!T || !W || !g_out || !esq_out) return CPD_ERR_INVALID_ARG;
-  if (!refine_pass_supported((int)dims[0], R)) return CPD_ERR_UNSUPPORTED;
+  if (!pass_ok(L, dims, R)) return CPD_ERR_UNSUPPORTED;
   RefinePassArgs pa{};
   pa.T = T; pa.L = L; pa.R = R; pa.W = W; pa.G = g_out; pa.esq = esq_out; pa.want_tsq = 1;
   for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = (l < L) ? dims[l] : 1;

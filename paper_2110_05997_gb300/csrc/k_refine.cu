@@ -24,32 +24,29 @@ __global__ void k_zero_pass(float* G, int n, double* esq, int want_tsq, const in
 }
 
 // Supported shapes: I1 <= 256 * SLOTS with RMAX * SLOTS <= 64 (I1 <= 1024 for
-// R <= 16, I1 <= 512 for R <= 32, I1 <= 256 for R <= 64).
-bool refine_pass_supported(int I1, int R) {
-  if (R <= 16) return I1 <= 1024;
-  if (R <= 32) return I1 <= 512;
-  return I1 <= 256;
+// R <= 16, I1 <= 512 for R <= 32, I1 <= 256 for R <= 64), fibre indices below
+// 2^31 and the pass's shared memory within one CTA's 227 KB.
+bool refine_pass_supported(int L, const long long* dims, int R) {
+  const long long I1 = dims[0];
+  if (R <= 16 ? I1 > 1024 : R <= 32 ? I1 > 512 : I1 > 256) return false;
+  long long nf = 1;
+  for (int l = 1; l < L; ++l) nf *= dims[l];
+  if (nf >= (1ll << 31)) return false;
+  return pass_smem(L, dims, R) <= (size_t)227 * 1024;
 }
 
 cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st) {
   int n = 0;
   for (int l = 0; l < a.L; ++l) n += (int)a.dims[l] * a.R;
-  if (!refine_pass_supported((int)a.dims[0], a.R)) return cudaErrorInvalidValue;
+  if (!refine_pass_supported(a.L, a.dims, a.R)) return cudaErrorInvalidValue;
   k_zero_pass<<<16, 256, 0, st>>>(a.G, n, a.esq, a.want_tsq, a.done);
   count_launch();
   const size_t smem = pass_smem(a.L, a.dims, a.R);
   long long nf = 1;
   for (int l = 1; l < a.L; ++l) nf *= a.dims[l];
-  if (nf >= (1ll << 31)) return cudaErrorInvalidValue;     // fibre indices are 32-bit
   const long long nbatch = (nf + kNB - 1) / kNB;
   const int threads = a.dims[0] >= 256 ? 256 : (int)((a.dims[0] + 31) / 32 * 32);
-  int per_sm = (int)((227 * 1024) / (smem + 1024));
-  const int by_threads = 2048 / threads;
-  if (per_sm > by_threads) per_sm = by_threads;
-  if (per_sm < 1) per_sm = 1;
-  long long blocks = nbatch < (long long)per_sm * 152 ? nbatch : (long long)per_sm * 152;
-  if (blocks < 1) blocks = 1;
-  return a.L == 3 ? launch_refine_pass3(a, smem, threads, blocks, st) : launch_refine_pass4(a, smem, threads, blocks, st);
+  return a.L == 3 ? launch_refine_pass3(a, smem, threads, nbatch, st) : launch_refine_pass4(a, smem, threads, nbatch, st);
 }
 
 // ---- the single-CTA step ----------------------------------------------------------

@@ -4,9 +4,9 @@
 
 namespace cpdk {
 
-cudaError_t launch_refine_pass3(const RefinePassArgs& a, size_t smem, int threads, long long blocks,
+cudaError_t launch_refine_pass3(const RefinePassArgs& a, size_t smem, int threads, long long nbatch,
                                  cudaStream_t st) {
-  return launch_pass_l<3>(a, smem, threads, blocks, st);
+  return launch_pass_l<3>(a, smem, threads, nbatch, st);
 }
 
 }  // namespace cpdk

@@ -149,7 +149,7 @@ struct RefinePassArgs {
   const int* done;            // skip when *done != 0 (refinement stopped)
 };
 cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st);
-bool refine_pass_supported(int I1, int R);
+bool refine_pass_supported(int L, const long long* dims, int R);
 
 struct RefineStepArgs {
   int L, R;

@@ -99,7 +99,12 @@ def test_compress_exact_low_multilinear_rank(cpd):
     assert np.linalg.norm(rec - T) <= 1e-5 * np.linalg.norm(T)
 
 
-@pytest.mark.parametrize("dims,R", [((50, 40, 30), 4), ((20, 18, 16, 14), 3), ((257, 3, 5), 2), ((7, 33, 65), 6)])
+# every padded rank (8, 12, 16, 32, 64), one to four rows per thread (I1 up
+# to 1024), orders 3 and 4, ragged last batches of fibres
+@pytest.mark.parametrize("dims,R", [((50, 40, 30), 4), ((20, 18, 16, 14), 3), ((257, 3, 5), 2), ((7, 33, 65), 6),
+                                    ((300, 20, 10), 10), ((200, 17, 9), 12), ((40, 30, 20), 16),
+                                    ((64, 9, 7), 20), ((33, 10, 6), 40), ((600, 5, 4), 3),
+                                    ((1024, 3, 3), 16), ((20, 18, 16, 14), 12), ((130, 7, 5, 3), 30)])
 def test_refine_eval_matches_oracle(cpd, dims, R):
     g = np.random.default_rng(sum(dims) + R)
     T = g.standard_normal(dims).astype(np.float32).astype(np.float64)
