@@ -354,11 +354,22 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
       CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
       if (refine_loop) *refine_loop = 1;
     } else {
+      // under profiling the host reads the stop flag after each step and
+      // launches no further iterations, as the graph loop does (the stage
+      // times then hold only the iterations that run)
+      const bool watch = profile_enabled() && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+                         cs == cudaStreamCaptureStatusNone;
       for (int j = 0; j <= o.refine_maxiter; ++j) {
         pa.want_tsq = (j == 0);
         PL("refine_pass", launch_refine_pass(pa, st));
         sa.j = j;
         PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+        if (watch) {
+          int done = 0;
+          CK(cudaMemcpyAsync(&done, p.rdone, sizeof(int), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (done) break;
+        }
       }
     }
     Wfinal = Wr;

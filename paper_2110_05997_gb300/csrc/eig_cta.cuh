@@ -399,12 +399,57 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
   return false;
 }
 
-// Z = G Q (G symmetric I x I, column-major; Q I x m): a thread computes four
-// columns of two rows (i and i + ceil(I/2)) with independent accumulators, so
-// each broadcast load of Q feeds two FMAs (shared-memory wavefronts, not FMAs,
-// bound this product).
-static __device__ void gram_times(const float* G, const float* Q, float* Z, int I, int m) {
-  const int mq = (m + 3) >> 2, Ih = (I + 1) >> 1;
+// Z = G Q (G symmetric I x I, column-major; Q I x m, column-major).
+// Shared-memory wavefronts, not FMAs, bound this product, so each thread
+// takes a 4 x 4 tile of Z: per k one 16-byte load of G's rows 4b..4b+3 and
+// one 16-byte broadcast load of Q's row k from the k-major copy Qt (stride
+// mp = m rounded up to 4, zero-padded) feed 16 FMAs.  Needs I % 4 == 0, a
+// 16-byte aligned G and TILED (the batched solver's small Grams keep the
+// scalar form and its registers); otherwise a thread computes four columns
+// of two rows (i and i + ceil(I/2)) with scalar loads.  Both forms sum over
+// k in the same order, so they give the same Z.
+template <bool TILED>
+static __device__ void gram_times(const float* G, const float* Q, float* Z, float* Qt, int I, int m) {
+  const int mp = (m + 3) & ~3, mq = mp >> 2;
+  if (TILED && (I & 3) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0) {
+    for (int e = threadIdx.x; e < I * mp; e += blockDim.x) {
+      const int k = e / mp, j = e - k * mp;
+      Qt[e] = j < m ? Q[(size_t)j * I + k] : 0.f;
+    }
+    __syncthreads();
+    const int Ib = I >> 2;
+    const float4* G4 = reinterpret_cast<const float4*>(G);
+    const float4* Q4 = reinterpret_cast<const float4*>(Qt);
+    for (int e = threadIdx.x; e < Ib * mq; e += blockDim.x) {
+      const int bi = e % Ib, c = e / Ib;
+      float acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < I; ++k) {
+        const float4 g = G4[(size_t)k * Ib + bi];
+        const float4 q = Q4[(size_t)k * mq + c];
+        const float gv[4] = {g.x, g.y, g.z, g.w}, qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(gv[u], qv[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = 4 * c + v;
+        if (j < m) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Z[(size_t)j * I + 4 * bi + u] = acc[u][v];
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int Ih = (I + 1) >> 1;
   for (int e = threadIdx.x; e < Ih * mq; e += blockDim.x) {
     const int i = e % Ih, j0 = (e / Ih) * 4, i2 = i + Ih;
     const bool two = i2 < I;
@@ -454,10 +499,14 @@ static __device__ void rayleigh(const float* Q, const float* Z, double* H, int I
 }
 
 
-__host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g) {
+// tiled: room for the k-major copy of Q that the tiled G Q product reads
+// (the eigen kernel, MMAX > 32; the batched solver's eig_run<32> has none).
+__host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g, bool tiled = true) {
   const int m = eig_m(I, P);
-  size_t base = 128 * sizeof(double) + 4 * (size_t)m * m * sizeof(double) + (size_t)m * m * sizeof(float) +
-                (size_t)((m + 3) & ~3) * sizeof(float) + 2 * (size_t)I * m * sizeof(float);
+  const size_t mp = (size_t)((m + 3) & ~3);
+  size_t base = 128 * sizeof(double) + 4 * (size_t)m * m * sizeof(double) +
+                (((size_t)m * m + 3) & ~(size_t)3) * sizeof(float) + mp * sizeof(float) +
+                (tiled ? (size_t)I * mp * sizeof(float) : 0) + 2 * (size_t)I * m * sizeof(float);
   return with_g ? base + (size_t)I * I * sizeof(float) : base;
 }
 
@@ -470,15 +519,18 @@ __host__ __device__ inline size_t eig_smem_bytes(int I, int P, bool with_g) {
 template <int MMAX = kMaxM>
 static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
   const int I = a.I, P = a.P, m = eig_m(I, P);
-  // layout: red(128 d) | H, V, W1, W2 (m*m d each) | Lf(m*m) | Cf(m) | Q(I*m) | Z(I*m) | G(I*I if it fits)
+  // layout: red(128 d) | H, V, W1, W2 (m*m d each) | Lf(m*m, to 4) | Cf(m, to 4) | Qt(I*mp)
+  //         | Q(I*m) | Z(I*m) | G(I*I if it fits); Lf, Qt and G start on 16 bytes
+  const int mp = (m + 3) & ~3;
   double* red = reinterpret_cast<double*>(smem_raw);
   double* H = red + 128;
   double* V = H + m * m;
   double* W1 = V + m * m;
   double* W2 = W1 + m * m;
   float* Lf = reinterpret_cast<float*>(W2 + m * m);
-  float* Cf = Lf + m * m;
-  float* Q = Cf + ((m + 3) & ~3);
+  float* Cf = Lf + ((m * m + 3) & ~3);
+  float* Qt = Cf + mp;
+  float* Q = Qt + (MMAX > 32 ? (size_t)I * mp : 0);
   float* Z = Q + (size_t)I * m;
   float* Gs = Z + (size_t)I * m;
   const bool g_in_smem = a.work == nullptr;
@@ -506,14 +558,14 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
       Q[e] = (splitmix64(a.seed, kStreamEig, (uint64_t)j * 1000003ull + i) >> 63) ? 1.f : -1.f;
     }
     __syncthreads();
-    gram_times(G, Q, Z, I, m);
+    gram_times<(MMAX > 32)>(G, Q, Z, Qt, I, m);
     double prev = -1.0;
     for (int it = 0; it < 30; ++it) {
       cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, it);
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) Z[e] = Q[e];
       __syncthreads();
       cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, 1000 + it);
-      gram_times(G, Q, Z, I, m);
+      gram_times<(MMAX > 32)>(G, Q, Z, Qt, I, m);
       float vf[1] = {0.f};
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) vf[0] = fmaf(Q[e], Z[e], vf[0]);
       double v[1];

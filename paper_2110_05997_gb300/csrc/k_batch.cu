@@ -146,7 +146,7 @@ __host__ __device__ inline StoreLayout store_layout(int dmax, int Rmax) {
 __host__ __device__ inline size_t batch_compress_smem(int dmax, int Rmax) {
   const int P = Rmax < dmax ? Rmax : dmax;
   return (size_t)g_floats(dmax) * 4 + (size_t)kGTile * kGLd * 4 + (size_t)dmax * P * 4 + 256 +
-         eig_smem_bytes(dmax, P, false);
+         eig_smem_bytes(dmax, P, false, false);
 }
 
 template <int TH>

@@ -4,6 +4,8 @@
 // to T).  Included by one translation unit per tensor order.
 #pragma once
 
+#include <mutex>
+
 #include "kernels.h"
 #include "solver.cuh"
 
@@ -357,22 +359,45 @@ inline size_t pass_smem(int L, const long long* dims, int R) {
 // Grid: every CTA resident at once (CTAs per SM by registers, shared memory
 // and threads, times the SM count), capped at the number of fibre batches
 // `nbatch`; each CTA strides over the batches.
+// The attributes and the resident-CTA count of the last (device, shared
+// memory, threads) an instantiation was launched with are kept, so repeated
+// launches of one shape make no host queries.
+struct PassLaunchCache {
+  std::mutex mu;
+  int dev = -1, threads = 0;
+  size_t smem = 0;
+  long long resident = 0;
+};
+
 template <int L, int RP, int SLOTS>
 inline cudaError_t launch_pass_t(const RefinePassArgs& a, size_t smem, int threads, long long nbatch,
                                  cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_refine_pass<L, RP, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static PassLaunchCache cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  // all of the unified L1 as shared memory, so that CTAs can share an SM
-  e = cudaFuncSetAttribute(k_refine_pass<L, RP, SLOTS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_pass<L, RP, SLOTS>, threads, smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  long long blocks = (long long)per_sm * sms;
+  long long resident = 0;
+  {
+    std::lock_guard<std::mutex> lk(cache.mu);
+    if (cache.dev == dev && cache.smem == smem && cache.threads == threads) resident = cache.resident;
+  }
+  if (resident == 0) {
+    e = cudaFuncSetAttribute(k_refine_pass<L, RP, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // all of the unified L1 as shared memory, so that CTAs can share an SM
+    e = cudaFuncSetAttribute(k_refine_pass<L, RP, SLOTS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_pass<L, RP, SLOTS>, threads, smem)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    resident = (long long)per_sm * sms;
+    std::lock_guard<std::mutex> lk(cache.mu);
+    cache.dev = dev; cache.smem = smem; cache.threads = threads; cache.resident = resident;
+  }
+  long long blocks = resident;
   if (blocks > nbatch) blocks = nbatch;
   if (blocks < 1) blocks = 1;
   k_refine_pass<L, RP, SLOTS><<<(unsigned)blocks, threads, smem, st>>>(a);
