@@ -207,10 +207,11 @@ def flat_tensor(T):
 
 
 def cpd_dgn_solve(T_flat, dims, R: int, opts: cpd_options | None = None, W0_flat=None,
-                  trace: bool = False, stream=None, workspace=None):
+                  trace: bool = False, stream=None, workspace=None, want_info: bool = True):
     """Run the whole method on the device tensor ``T_flat`` (column-major flat,
     FP32 or FP64).  Returns (W list of I_l x R unit-column tensors, lambda,
-    info dict, trace tensor or None)."""
+    info dict, trace tensor or None).  With want_info=False no info record is
+    read (the call does not synchronise the stream) and the info is None."""
     import torch
     opts = opts or cpd_default_options()
     dev = T_flat.device
@@ -225,13 +226,13 @@ def cpd_dgn_solve(T_flat, dims, R: int, opts: cpd_options | None = None, W0_flat
         workspace = _workspace(cpd_workspace_size(dims, R, opts), dev)
     info = cpd_info()
     st = lib().cpd_dgn_solve(_ptr(T_flat), dtype, len(dims), _dims(dims), int(R), C.byref(opts),
-                             _ptr(W0_flat), _ptr(W), _ptr(lam), C.byref(info), _ptr(tr),
-                             _ptr(workspace), workspace.numel(), _stream(stream))
+                             _ptr(W0_flat), _ptr(W), _ptr(lam), C.byref(info) if want_info else None,
+                             _ptr(tr), _ptr(workspace), workspace.numel(), _stream(stream))
     _check("cpd_dgn_solve", st)
     trv = None
     if tr is not None:
         trv = tr.reshape(-1, TRACE_FIELDS)
-    return _stacked_split(W, dims, R), lam, info.as_dict(), trv
+    return _stacked_split(W, dims, R), lam, (info.as_dict() if want_info else None), trv
 
 
 def cpd_compress(T_flat, dims, R: int, opts: cpd_options | None = None, stream=None):

@@ -63,7 +63,8 @@ size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_sm
 // In a graph loop (use_cond) every exit sets the loop condition: 0 once the
 // refinement has stopped or j = maxiter, else 1; j comes from the state's
 // counter, so the body's launch arguments are the same in every iteration.
-template <int L>
+// RP > 0: ranks up to RP take the row-wise CG (pcg_rows), else pcg.
+template <int L, int RP>
 __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   if (*a.done) {
     if (a.use_cond && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
@@ -147,7 +148,9 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   grams_pi<L>(s, b);                           // its first barrier publishes s_maxit
   regularize<L>(s, b, mu);
   const int maxit = s_maxit;
-  const int its = pcg<L>(s, b, mu, maxit, a.tol);
+  int its;
+  if constexpr (RP > 0) its = pcg_rows<L, RP>(s, b, mu, maxit, a.tol);
+  else its = pcg<L>(s, b, mu, maxit, a.tol);
   double pred_drop, step;
   finish_step<L>(s, b, pred_drop, step);
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) a.W[j] = b.W[j];
@@ -159,14 +162,25 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   }
 }
 
-cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st) {
-  const void* fn = (a.L == 3) ? (const void*)k_refine_step<3> : (const void*)k_refine_step<4>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int L, int RP>
+cudaError_t launch_step_t(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_refine_step<L, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (a.L == 3) k_refine_step<3><<<1, threads, smem, st>>>(a);
-  else k_refine_step<4><<<1, threads, smem, st>>>(a);
+  k_refine_step<L, RP><<<1, threads, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t launch_step_l(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st) {
+  if (a.R <= 8) return launch_step_t<L, 8>(a, threads, smem, st);
+  if (a.R <= 12) return launch_step_t<L, 12>(a, threads, smem, st);
+  if (a.R <= 16) return launch_step_t<L, 16>(a, threads, smem, st);
+  return launch_step_t<L, 0>(a, threads, smem, st);
+}
+
+cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st) {
+  return a.L == 3 ? launch_step_l<3>(a, threads, smem, st) : launch_step_l<4>(a, threads, smem, st);
 }
 
 __global__ void k_refine_init(RefineState* s, const DevResult* core, int* done) {

@@ -225,6 +225,95 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
   return its;
 }
 
+// The PCG of pcg() with the last phase of Theorem "Hv" taken row by row: a
+// thread forms the R entries (l, i, 0..R-1) of one row of block l together
+// (RP >= R accumulators), loading V^(l)[i, t] and W^(l)[i, t] once per t and
+// the rows t of Pi^(l) and Ym^(l) as broadcasts, half the shared-memory loads
+// of one entry at a time.  Every entry sums in the order of hv_entry, so z is
+// the same as in pcg(); the partial sums of p^T z are taken per thread over
+// its rows (another order).  For blocks with long columns (the refinement
+// step on the full tensor).
+template <int L, int RP>
+__device__ int pcg_rows(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const int n = s.n, R = s.R, RR = R * R;
+  int nrows = 0;
+#pragma unroll
+  for (int l = 0; l < L; ++l) nrows += s.d[l];
+  float v[1] = {0.f};
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    const float m = b.msq[l * R + r];
+    const float rv = m * b.G[j];
+    b.Rr[j] = rv; b.P[j] = rv; b.X[j] = 0.f; b.Tmp[j] = m * rv;
+    v[0] = fmaf(rv, rv, v[0]);
+  }
+  float rr0[1];
+  block_sum_f<1>(v, rr0, b.red);
+  float rr = rr0[0];
+  int its = 0;
+  for (int it = 0; it < maxit; ++it) {
+    hv_xy<L>(s, b, b.Tmp);
+    float pzf[1] = {0.f};
+    const float muf = (float)mu;
+    for (int row = threadIdx.x; row < nrows; row += blockDim.x) {
+      int l = 0, i = row;
+      while (l < L - 1 && i >= s.d[l]) { i -= s.d[l]; ++l; }
+      const float* P1 = b.Pi2 + (l * L + l) * RR;
+      const float* Y = b.Ym + l * RR;
+      const int d = s.d[l], base = s.off[l] + i;
+      float z[RP];
+#pragma unroll
+      for (int r = 0; r < RP; ++r) z[r] = 0.f;
+      for (int t = 0; t < R; ++t) {
+        const float vt = b.Tmp[base + t * d], wt = b.W[base + t * d];
+        const float* p1 = P1 + t * R;
+        const float* y = Y + t * R;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+          if (r < R) {
+            z[r] = fmaf(vt, p1[r], z[r]);
+            z[r] = fmaf(wt, y[r], z[r]);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        if (r < R) {
+          const int j = base + r * d, q = l * R + r;
+          const float zz = b.msq[q] * (z[r] + muf * b.gam[q] * b.Tmp[j]);
+          b.Z[j] = zz;
+          pzf[0] = fmaf(b.P[j], zz, pzf[0]);
+        }
+      }
+    }
+    float pz[1];
+    block_sum_f<1>(pzf, pz, b.red);
+    if (!(pz[0] > 0.f)) break;
+    const float af = rr / pz[0];
+    float rnf[1] = {0.f};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      b.X[j] = fmaf(af, b.P[j], b.X[j]);
+      const float rv = fmaf(-af, b.Z[j], b.Rr[j]);
+      b.Rr[j] = rv;
+      rnf[0] = fmaf(rv, rv, rnf[0]);
+    }
+    float rn[1];
+    block_sum_f<1>(rnf, rn, b.red);
+    const float bf = rr > 0.f ? rn[0] / rr : 0.f;
+    rr = rn[0];
+    its = it + 1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      int l, i, r; decode_j<L>(s, j, l, i, r);
+      const float pv = fmaf(bf, b.P[j], b.Rr[j]);
+      b.P[j] = pv;
+      b.Tmp[j] = b.msq[l * R + r] * pv;
+    }
+    __syncthreads();
+    if ((double)rr < tol) break;
+  }
+  return its;
+}
+
 // The same PCG when every thread owns at most one unknown (n <= blockDim.x):
 // x, r, p, the preconditioner entry and the decoded index stay in registers
 // and only M^{-1/2} p (the vector J^T J is applied to) goes through shared
