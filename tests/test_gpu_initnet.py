@@ -257,7 +257,7 @@ def test_trained_network_gains_over_mlsvd_start(cpd):
     The learned start (taken when its residual is below half the MLSVD
     start's) must be taken for some problems and must not cost iterations
     (<= 3% more) or converged problems (<= 1.5 points fewer); the
-    oracle-checked batched solver is the judge.  Measured on a GB300 with
+    oracle-checked batched solver decides.  Measured on a GB300 with
     196608 training problems: taken for ~10% of 4096 held-out problems, mean
     iterations 21.04 -> 20.93, converged 0.785 -> 0.782 -- no real gain.
     Taking it whenever its residual is the smaller one (78% of problems)
