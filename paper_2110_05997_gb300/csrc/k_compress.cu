@@ -161,6 +161,73 @@ __global__ void __launch_bounds__(256) k_project_first(const float* __restrict__
   }
 }
 
+// First mode (a = 1), tiled: a CTA copies kPC consecutive columns of T_(1)
+// (contiguous, b floats each) into shared memory with a row stride of b + 1
+// (asynchronous 4-byte copies; odd stride, so the column reads below are free
+// of bank conflicts), thread t takes column t and forms its rk outputs from a
+// j-major copy of U (RP floats per row j, zero beyond rk; 16-byte broadcast
+// loads), summing over j in order.
+constexpr int kPC = 128;
+
+template <int RP>
+__global__ void __launch_bounds__(kPC) k_project_tiled(const float* __restrict__ T, int b, long long c,
+                                                        const float* __restrict__ U, const int* dev_rank,
+                                                        float* Y) {
+  extern __shared__ __align__(16) float sm[];
+  float* Ut = sm;                                   // b x RP, j-major
+  float* tile = Ut + (size_t)b * RP;                // kPC x (b + 1)
+  const int rk = *dev_rank;                         // <= RP (checked by the launcher's bound)
+  const long long k0 = (long long)blockIdx.x * kPC;
+  const int nc = (int)((c - k0) < kPC ? (c - k0) : kPC);
+  const float* src = T + (size_t)k0 * b;
+  for (int col = 0; col < nc; ++col) {
+    for (int j = threadIdx.x; j < b; j += kPC) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + (size_t)col * (b + 1) + j);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src + (size_t)col * b + j) : "memory");
+    }
+  }
+  for (int e = threadIdx.x; e < b * RP; e += kPC) {
+    const int j = e / RP, p = e - j * RP;
+    Ut[e] = p < rk ? U[(size_t)p * b + j] : 0.f;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < nc) {
+    float acc[RP];
+#pragma unroll
+    for (int p = 0; p < RP; ++p) acc[p] = 0.f;
+    const float* x = tile + (size_t)t * (b + 1);
+    const float4* u4 = reinterpret_cast<const float4*>(Ut);
+#pragma unroll 4
+    for (int j = 0; j < b; ++j) {
+      const float xv = x[j];
+#pragma unroll
+      for (int q = 0; q < RP / 4; ++q) {
+        const float4 u = u4[j * (RP / 4) + q];
+        acc[4 * q] = fmaf(u.x, xv, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(u.y, xv, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(u.z, xv, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(u.w, xv, acc[4 * q + 3]);
+      }
+    }
+    float* y = Y + (size_t)rk * (k0 + t);
+#pragma unroll
+    for (int p = 0; p < RP; ++p)
+      if (p < rk) y[p] = acc[p];
+  }
+}
+
+template <int RP>
+cudaError_t launch_project_tiled(const float* T, int b, long long c, const float* U, const int* dev_rank,
+                                 float* Y, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_project_tiled<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_project_tiled<RP><<<(unsigned)((c + kPC - 1) / kPC), kPC, smem, st>>>(T, b, c, U, dev_rank, Y);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // General mode: one warp per (i, k) of the (a, c) indices; lanes stride j,
 // 16 outputs per pass, warp reductions.
 __global__ void __launch_bounds__(256) k_project_gen(const float* __restrict__ T, View3 v,
@@ -202,6 +269,16 @@ __global__ void __launch_bounds__(256) k_project_gen(const float* __restrict__ T
 
 cudaError_t launch_project(const float* T, View3 v, long long a_max, const float* U,
                            const int* dev_rank, int rmax, float* Y, cudaStream_t st) {
+  if (v.a_host == 1 && v.dev_ranks == nullptr && rmax <= 16) {
+    const int rp = rmax <= 4 ? 4 : rmax <= 8 ? 8 : rmax <= 12 ? 12 : 16;
+    const size_t smem = ((size_t)v.b * rp + (size_t)kPC * (v.b + 1)) * sizeof(float);
+    if (smem <= 112 * 1024 + 512 && v.c < (1ll << 40)) {     // two CTAs per SM
+      if (rp == 4) return launch_project_tiled<4>(T, (int)v.b, v.c, U, dev_rank, Y, smem, st);
+      if (rp == 8) return launch_project_tiled<8>(T, (int)v.b, v.c, U, dev_rank, Y, smem, st);
+      if (rp == 12) return launch_project_tiled<12>(T, (int)v.b, v.c, U, dev_rank, Y, smem, st);
+      return launch_project_tiled<16>(T, (int)v.b, v.c, U, dev_rank, Y, smem, st);
+    }
+  }
   if (v.a_host == 1 && v.dev_ranks == nullptr) {
     const size_t smem = (size_t)v.b * rmax * sizeof(float);
     if (smem <= 200 * 1024) {
