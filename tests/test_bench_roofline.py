@@ -1,0 +1,57 @@
+"""Host logic of bench.py's roofline entries (no GPU): the algorithmic bytes
+and flops per launch that the fractions divide by, and the traffic record's
+tie to the kernels' sources."""
+import json
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PK = {"hbm": 6773.2, "sm_max_mhz": 2070}
+INFO = {"core_dims": [10, 10, 10, 0], "iters": 26, "cg_total": 202}
+
+
+def test_refine_pass_bytes_are_one_read_of_t_and_the_factors():
+    import bench
+    r = bench.algorithmic("refine_pass", (200, 200, 200), 10, INFO, 0.05, PK, 2070)
+    # T once (32 MB) plus W read and the gradient written (2 x 10 x 600 floats)
+    assert r["algorithmic_per_launch"] == 4.0 * 200 ** 3 + 4.0 * 2 * 10 * 600
+    assert r["bound"] == "hbm" and r["peak"] == PK["hbm"]
+    assert abs(r["achieved"] - r["algorithmic_per_launch"] / 0.05e-3 / 1e9) < 1e-6
+
+
+def test_tensor_core_gram_reads_the_tensor_once():
+    import bench
+    r = bench.algorithmic("gram_bf16_tc", (200, 200, 200), 10, INFO, 0.03, PK, 2070)
+    assert r["algorithmic_per_launch"] == 4.0 * 200 ** 3
+    assert r["flops"] == 2.0 * 200 * 200 ** 3
+
+
+@pytest.mark.parametrize("bf16,expected", [
+    # modes 2 and 3 on the truncated 10x200x200 and 10x10x200 tensors
+    (True, (2 * 200 * (10 * 200 * 200) + 2 * 200 * (10 * 10 * 200)) / 2),
+    # with mode 1 on the CUDA cores as well: the full tensor's first Gram too
+    (False, (2 * 200 * 200 ** 3 + 2 * 200 * (10 * 200 * 200) + 2 * 200 * (10 * 10 * 200)) / 3),
+])
+def test_fp32_gram_flops_follow_the_sequential_truncation(bf16, expected):
+    import bench
+    r = bench.algorithmic("gram_fp32", (200, 200, 200), 10, INFO, 0.03, PK, 2070, gram_bf16=bf16)
+    assert abs(r["algorithmic_per_launch"] - expected) < 1e-6 * expected
+    assert r["frac"] < 1.0
+
+
+def test_traffic_record_is_reported_only_for_unchanged_sources(tmp_path, monkeypatch):
+    import bench
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        rec = json.load(fh)
+    for stage, v in rec.items():
+        assert stage in bench.STAGE_SOURCES and v["dram_bytes_per_launch"] > 0
+        assert "--clock-control none" in v["capture"]
+    # a record whose hash is not the sources' is ignored (reported as null)
+    stale = {k: dict(v, sources_sha256="0" * 64) for k, v in rec.items()}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(stale))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sources_sha256", lambda stage: "1" * 64)
+    for stage in stale:
+        assert bench.measured_traffic(stage) is None
