@@ -35,15 +35,21 @@ __global__ void __launch_bounds__(256) k_gram_simt(const float* __restrict__ T, 
   const long long q1 = q0 + chunk < K ? q0 + chunk : K;
   if (q0 >= q1) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // offsets i + a b k of the K-step's kGK rows q = (i, k), one division each
+  // (by kGK threads) instead of one per loaded element; -1 past the chunk
+  __shared__ long long qoff[kGK];
   float acc[4][4] = {};
   for (long long qb = q0; qb < q1; qb += kGK) {
+    if (threadIdx.x < kGK) {
+      const long long q = qb + threadIdx.x;
+      qoff[threadIdx.x] = q < q1 ? (q % a) + a * b * (q / a) : -1;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
       const int kk = e / kGT, jj = e - kk * kGT;
-      const long long q = qb + kk;
+      const long long base = qoff[kk];
       float xa = 0.f, xb = 0.f;
-      if (q < q1) {
-        const long long i = q % a, k = q / a;
-        const long long base = i + a * b * k;
+      if (base >= 0) {
         const long long ja = (long long)ti * kGT + jj, jb = (long long)tj * kGT + jj;
         if (ja < b) xa = __ldg(T + base + a * ja);
         if (jb < b) xb = __ldg(T + base + a * jb);
