@@ -209,7 +209,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
         PL("gram_fp32", launch_gram_simt(cur, v, a_max, p.G, st));
       }
       EigArgs ea{p.G, p.idims[l], p.P[l], p.U + offU, p.sigma + offS, p.core_dims_dev + l,
-                 o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work};
+                 o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work,
+                 o.gram_precision == CPD_GRAM_BF16 ? 1 : 0};
       PL("eig", launch_eig(ea, st));
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
       PL("project", launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
@@ -232,7 +233,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       else
         PL("gram_fp32", launch_gram_simt(T, v, a, p.G, st));
       EigArgs ea{p.G, p.idims[l], p.P[l], p.U + offU, p.sigma + offS, p.core_dims_dev + l,
-                 o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work};
+                 o.mlsvd_tol, L, o.seed + 7919ull * (uint64_t)l, p.eig_work,
+                 o.gram_precision == CPD_GRAM_BF16 ? 1 : 0};
       PL("eig", launch_eig(ea, st));
       offU += (size_t)p.idims[l] * p.P[l];
       offS += p.P[l];

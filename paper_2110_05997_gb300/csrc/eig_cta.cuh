@@ -186,7 +186,7 @@ static __device__ void small_gemm(const double* A, bool at, const double* B, dou
 //      work inside clusters of close eigenvalues.
 // W1, W2: m x m FP64 scratch each.  On return H is diagonal (the eigenvalues)
 // and the columns of V are the eigenvectors.
-static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, double* W2) {
+static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, double* W2, bool polish = true) {
   float* Hf = reinterpret_cast<float*>(W1);
   float* Vf = Hf + m * m;
   float* Hf2 = reinterpret_cast<float*>(W2);
@@ -204,6 +204,12 @@ static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, doubl
     jacobi_sweep<float>(Hf, Hf2, Vf, m, 0.f);
   }
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) V[e] = (double)Vf[e];
+  if (!polish) {
+    // the FP32 decomposition is as accurate as the (BF16-rounded) Gram
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) H[e] = (double)Hf[e];
+    __syncthreads();
+    return;
+  }
   __syncthreads();
   small_gemm(V, true, V, W2, m, true);          // W2 = (3I - V0^T V0) / 2
   small_gemm(V, false, W2, W1, m, false);       // W1 = V0 W2
@@ -546,7 +552,7 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     // the whole space: Jacobi on G itself (m = I <= P + 6)
     for (int e = threadIdx.x; e < I * I; e += blockDim.x) H[e] = (double)G[e];
     __syncthreads();
-    jacobi_eig(H, V, I, W1, W2);
+    jacobi_eig(H, V, I, W1, W2, a.fp32_only == 0);
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) {
       const int j = e / I, i = e - j * I;
       Q[j * I + i] = (float)V[i * m + j];
@@ -575,7 +581,7 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     }
     // Rayleigh-Ritz: H = Q^T G Q, eig, U = Q V
     rayleigh(Q, Z, H, I, m);
-    jacobi_eig(H, V, m, W1, W2);
+    jacobi_eig(H, V, m, W1, W2, a.fp32_only == 0);
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) {
       const int j = e / I, i = e - j * I;
       float s = 0.f;

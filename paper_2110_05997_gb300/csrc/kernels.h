@@ -115,6 +115,7 @@ struct EigArgs {
   int L;
   uint64_t seed;
   float* work;                // global scratch when G does not fit shared memory
+  int fp32_only;              // 1: no FP64 polishing (the Gram itself is BF16-rounded)
 };
 cudaError_t launch_eig(const EigArgs& a, cudaStream_t st);
 size_t eig_work_floats(int I, int P);
