@@ -118,3 +118,31 @@ def test_workspace_size_grows_with_problem(cpd):
     b = cpd.cpd_workspace_size((200, 200, 200), 10, o)
     assert 0 < a < b
     assert cpd.cpd_workspace_size((4, 4, 4, 4, 4), 2, o) == 0
+
+
+def test_refinement_shape_limits_are_checked_before_launch(cpd):
+    """The refinement pass keeps one row of the first mode per thread (up to 4
+    rows for ranks <= 16), the factor blocks of the other modes twice and
+    I_1 x (33 + padded R) floats in one CTA's shared memory; shapes beyond
+    that are refused up front (nothing is launched, the dummy pointers are
+    never touched)."""
+    L = cpd.lib()
+    info = cpd.cpd_info()
+    nul = C.c_void_p(0)
+    dummy = C.c_void_p(0x1000)
+
+    def solve(dims, R, refine):
+        o = cpd.cpd_default_options(refine_maxiter=refine)
+        return L.cpd_dgn_solve(dummy, 0, len(dims), cpd._dims(dims), R, C.byref(o), nul, dummy, dummy,
+                               C.byref(info), nul, dummy, 1 << 20, nul)
+
+    def evaluate(dims, R):
+        return L.cpd_refine_eval(dummy, len(dims), cpd._dims(dims), R, dummy, dummy, dummy, nul, 0, nul)
+
+    for dims, R in [((2000, 4, 4), 2),            # I_1 above 1024
+                    ((600, 4, 4), 20),            # ranks 17..32: I_1 up to 512
+                    ((300, 4, 4), 40),            # ranks 33..64: I_1 up to 256
+                    ((100, 4000, 4000), 16),      # factor blocks of modes 2..3 beyond shared memory
+                    ((8, 2, 2, 2), 65)]:          # rank above the maximum (refused earlier)
+        assert solve(dims, R, 5) == -6, (dims, R)
+        assert evaluate(dims, R) == -6, (dims, R)
