@@ -285,6 +285,67 @@ def init_random(seed: int, dims, R: int):
     return Ws
 
 
+# --- updates and stopping conditions (Sec. 4.1.3) -----------------------------
+
+def window_constant(maxiter: int) -> int:
+    """c = 1 + ceil(maxiter/10), the batch length of stop tests 5 and 6."""
+    return 1 + math.ceil(maxiter / 10)
+
+
+def gain_ratio(F_old: float, F_new: float, pred_drop: float) -> float:
+    """Gain ratio of Sec. 3.5.2 / Sec. 4.1.3 "Updates": actual over predicted
+    decrease, pred_drop = F_old - ½||f + Jx||^2 (reading R5).  A
+    non-positive predicted decrease gives gain 0 (the step is not trusted)."""
+    return (F_old - F_new) / pred_drop if pred_drop > 0 else 0.0
+
+
+def update_mu(mu: float, gain: float) -> float:
+    """Damping update chosen in Sec. 4.1.3 "Updates": mu <- 3 mu when the
+    gain is below 0.25, mu <- mu/3 when it is above 0.75, else unchanged."""
+    if gain < 0.25:
+        return 3.0 * mu
+    if gain > 0.75:
+        return mu / 3.0
+    return mu
+
+
+def stop_reason(errs, k: int, step: float, grad_inf: float, norm: float, tol: float,
+                maxiter: int) -> int:
+    """The seven stopping conditions of Sec. 4.1.3, in the printed order, plus
+    the iteration cap; returns the number of the first that holds (0: none).
+
+    errs[j] is the relative error ||S - S^(j)|| / ||S|| after iteration j
+    (errs[0] at the start), k >= 1 the current iteration, step = ||w^(k-1) -
+    w^(k)||, grad_inf = ||grad F(w^(k))||_inf, norm = ||S|| of the tensor
+    being decomposed.  Conditions 5 and 6 are evaluated only when k is a
+    multiple of c = 1 + ceil(maxiter/10) and k > 2c, with the printed sums
+    over j = k-2c..k-c and j = k-c..k (c + 1 terms each), divided by c."""
+    e = errs[k]
+    c = window_constant(maxiter)
+    if e < tol:
+        return 1
+    if step < tol:
+        return 2
+    if abs(errs[k - 1] - errs[k]) < tol:
+        return 3
+    if grad_inf < tol:
+        return 4
+    batch = k % c == 0 and k > 2 * c
+    if batch:
+        avg_old = sum(errs[j] for j in range(k - 2 * c, k - c + 1)) / c
+        avg_new = sum(errs[j] for j in range(k - c, k + 1)) / c
+        if avg_old - avg_new < tol:
+            return 5
+        avg_impr = sum(abs(errs[j - 1] - errs[j]) for j in range(k - c, k + 1)) / c
+        if avg_impr < 1e-3 * avg_new:
+            return 6
+    if e > max(1.0, norm ** 2) / (1e-16 + tol):
+        return 7
+    if k == maxiter:
+        return 8
+    return 0
+
+
 # --- the dGN loop (Sec. 4.1.3) -------------------------------------------------
 
 def dgn(T: np.ndarray, W0, opts: Options, mu0: float | None = None, k0: int = 0,
@@ -300,7 +361,6 @@ def dgn(T: np.ndarray, W0, opts: Options, mu0: float | None = None, k0: int = 0,
     F = 0.5 * float(np.sum(f * f))
     g = neg_gradient(f, Ws)
     errs = [math.sqrt(2.0 * F) / normT if normT > 0 else 0.0]
-    c = 1 + math.ceil(opts.maxiter / 10)
     stop, k, cg_total = 8, 0, 0
     grad_inf = max(float(np.max(np.abs(x))) for x in g)
     for k in range(1, opts.maxiter + 1):
@@ -318,11 +378,8 @@ def dgn(T: np.ndarray, W0, opts: Options, mu0: float | None = None, k0: int = 0,
         f = residual(T, Ws)
         F_new = 0.5 * float(np.sum(f * f))
         g = neg_gradient(f, Ws)
-        gain = (F - F_new) / pred_drop if pred_drop > 0 else 0.0
-        if gain < 0.25:
-            mu *= 3.0
-        elif gain > 0.75:
-            mu /= 3.0
+        gain = gain_ratio(F, F_new, pred_drop)
+        mu = update_mu(mu, gain)
         e = math.sqrt(2.0 * F_new) / normT if normT > 0 else 0.0
         errs.append(e)
         grad_inf = max(float(np.max(np.abs(v))) for v in g)
@@ -330,26 +387,7 @@ def dgn(T: np.ndarray, W0, opts: Options, mu0: float | None = None, k0: int = 0,
         if trace is not None:
             trace.append(dict(k=k0 + k, rel_err=e, mu=mu, gain=gain, cg=its,
                               step=step, grad_inf=grad_inf))
-        stop = 0
-        if e < tol:
-            stop = 1
-        elif step < tol:
-            stop = 2
-        elif abs(errs[k - 1] - errs[k]) < tol:
-            stop = 3
-        elif grad_inf < tol:
-            stop = 4
-        elif k % c == 0 and k > 2 * c and \
-                sum(errs[k - 2 * c:k - c + 1]) / c - sum(errs[k - c:k + 1]) / c < tol:
-            stop = 5
-        elif k % c == 0 and k > 2 * c and \
-                sum(abs(errs[j - 1] - errs[j]) for j in range(k - c, k + 1)) / c \
-                < 1e-3 * sum(errs[k - c:k + 1]) / c:
-            stop = 6
-        elif e > max(1.0, normT ** 2) / (1e-16 + tol):
-            stop = 7
-        elif k == opts.maxiter:
-            stop = 8
+        stop = stop_reason(errs, k, step, grad_inf, normT, tol, opts.maxiter)
         if stop:
             break
     info = dict(iters=k, stop=stop, rel_err=errs[-1], mu=mu, grad_inf=grad_inf,
