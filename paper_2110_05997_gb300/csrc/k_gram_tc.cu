@@ -31,16 +31,18 @@
 #include <utility>
 
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace cpdk {
 namespace {
+
+using namespace tc;
 
 constexpr int kKT = 64;                   // unfolding columns per step
 constexpr int kConv = 256;                // converting threads (warps 0-7; warps 0-3 read tensor memory back)
 constexpr int kIssuer = 256;              // thread issuing the bulk copies and the MMAs (warp 8)
 constexpr int kThreads = kConv + 32;
 constexpr int kMaxStages = 4;
-constexpr int kSpinLimit = 1 << 21;       // bounded mbarrier polling
 constexpr int kCluster = 8;               // CTAs whose partial Grams are summed on chip
 
 struct TcArgs {
@@ -52,53 +54,6 @@ struct TcArgs {
   int vec4;             // G rows may be added as float4
   unsigned tmem_cols;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kSpinLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// tcgen05 shared-memory matrix descriptor for a K-major tile whose rows are
-// 128 bytes, stored as 8-row groups of 1024 bytes with the 128-byte swizzle.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);     // start address
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
-  d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: one 8-row group
-  d |= (uint64_t)1 << 46;                        // descriptor version
-  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
-  return d;
-}
-
-// tcgen05 instruction descriptor, kind::f16: BF16 A and B (both K-major),
-// FP32 accumulator, M x N tile.
-__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Eight FP32 values -> eight BF16 (round to nearest even), packed in order.
-__device__ __forceinline__ uint4 pack_bf16x8(const float (&f)[8]) {
-  uint4 w;
-  __nv_bfloat162 h0 = __floats2bfloat162_rn(f[0], f[1]), h1 = __floats2bfloat162_rn(f[2], f[3]);
-  __nv_bfloat162 h2 = __floats2bfloat162_rn(f[4], f[5]), h3 = __floats2bfloat162_rn(f[6], f[7]);
-  w.x = *reinterpret_cast<uint32_t*>(&h0); w.y = *reinterpret_cast<uint32_t*>(&h1);
-  w.z = *reinterpret_cast<uint32_t*>(&h2); w.w = *reinterpret_cast<uint32_t*>(&h3);
-  return w;
-}
 
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];

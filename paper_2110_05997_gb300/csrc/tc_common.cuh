@@ -1,0 +1,178 @@
+// Shared plumbing of the tcgen05 (5th-generation tensor core) kernels:
+// shared-memory addresses, bounded mbarrier waits, the shared-memory matrix
+// descriptor of the 128-byte-swizzled K-major layout, the kind::f16
+// instruction descriptor, BF16 packing, and the tensor-memory allocation
+// and fence instructions.  Written from the PTX ISA's descriptions of
+// tcgen05.mma, tcgen05.alloc / dealloc, mbarrier and cp.async.bulk.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace cpdk {
+namespace tc {
+
+// Default poll budget of a bounded mbarrier wait (iterations of try_wait,
+// each of which may itself suspend for a hardware-chosen interval).
+constexpr long long kSpinDefault = 1ll << 21;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Poll the phase `parity` of the mbarrier at shared address `bar` at most
+// `limit` times; false when the phase did not complete within the budget.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kSpinDefault) {
+  for (long long it = 0; it < limit; ++it)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand whose rows are 128
+// bytes (64 BF16), stored as 8-row groups of 1024 bytes with the 128-byte
+// swizzle: start address >> 4 (bits 0-13), stride between 8-row groups
+// (bits 32-45, in 16-byte units), descriptor version 1 (bit 46), swizzle
+// mode 2 = 128 B (bits 61-63).  The leading byte offset is unused for this
+// layout and set to 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
+// 4-5 = 1), BF16 A (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major,
+// N >> 3 in bits 17-22 and M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor for an MN-major operand in the 128-byte
+// swizzle: each 128-byte row holds 64 consecutive BF16 of the M (or N)
+// dimension for one K index, 8 K-rows form a 1024-byte swizzle atom.  `lbo`
+// is the byte distance between consecutive 64-element groups along M/N
+// (bits 16-29), the stride byte offset (bits 32-45) the distance between
+// consecutive groups of 8 K-rows.
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16 (BF16 operands, FP32 accumulator) with
+// the operand majors: bit 15 set = A is MN-major, bit 16 set = B is MN-major.
+__host__ __device__ constexpr uint32_t mma_idesc_major(int M, int N, bool a_mn, bool b_mn) {
+  return mma_idesc(M, N) | (a_mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u);
+}
+
+// Byte offset, inside a 1024-byte-aligned tile of 128-byte rows with the
+// 128-byte swizzle, of byte `b` (< 128) of row `row`: the 16-byte chunk index
+// is XORed with the row's position in its group of 8 rows.
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t b) {
+  return row * 128u + ((((b >> 4) ^ (row & 7u)) << 4) | (b & 15u));
+}
+
+// Eight FP32 values -> eight BF16 (round to nearest even), packed in order.
+__device__ __forceinline__ uint4 pack_bf16x8(const float (&f)[8]) {
+  uint4 w;
+  __nv_bfloat162 h0 = __floats2bfloat162_rn(f[0], f[1]), h1 = __floats2bfloat162_rn(f[2], f[3]);
+  __nv_bfloat162 h2 = __floats2bfloat162_rn(f[4], f[5]), h3 = __floats2bfloat162_rn(f[6], f[7]);
+  w.x = *reinterpret_cast<uint32_t*>(&h0); w.y = *reinterpret_cast<uint32_t*>(&h1);
+  w.z = *reinterpret_cast<uint32_t*>(&h2); w.w = *reinterpret_cast<uint32_t*>(&h3);
+  return w;
+}
+
+// Eight consecutive 32-bit columns of this thread's tensor-memory lane (the
+// 32x32b shape: warp w reads lanes 32 (w % 4) .. + 31, thread t lane + t),
+// starting at `taddr`; completes at the next tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Tensor-memory allocation of `cols` columns by one whole warp; the base
+// address is written to the shared word at `slot`.
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Make generic-proxy shared-memory writes visible to the async proxy (the
+// tensor core and the bulk-copy engine).
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// tcgen05.mma kind::f16 with the accumulator in tensor memory at `tmem`:
+// D (+)= A * B^T, A and B from shared-memory descriptors; accumulate = 0
+// overwrites D.
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive once on the mbarrier `bar` when every tcgen05.mma this thread issued
+// before has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+}  // namespace tc
+}  // namespace cpdk
