@@ -99,6 +99,18 @@ typedef struct {
   int refine_maxiter;   /* dGN iterations on T after uncompression (0 = none)   */
   uint64_t seed;        /* SplitMix64 seed for cg_maxiter (stream 1) and init    */
   int block_threads;    /* threads of the single-CTA solver kernels (0 = auto)   */
+  double mu_min;        /* 1e-5: floor of the damping parameter after each update.
+                           The solvers run the CG in FP32; once mu falls far below
+                           the FP32 unit roundoff (~6e-8) relative to J^T J, the
+                           rounding of J^T J v is amplified by ~1/mu along the
+                           scaling null space of J^T J (Theorem "J^T J is
+                           singular", Sec. 3.5) and the step overflows.  The floor
+                           keeps that amplification below ~1e-2.  0 = the thesis's
+                           rule alone (mu x3 / mu /3, Sec. 4.1.3 "Updates"). */
+  long long timeout_cycles;  /* bound of every device-side wait on an mbarrier of
+                           the tensor-core kernels, in SM clock cycles (0 = the
+                           default of 2^31 cycles, about one second); a wait that
+                           runs out ends the call with CPD_ERR_TIMEOUT */
 } cpd_options;
 
 /* Outcome of one CPD. */
@@ -192,7 +204,9 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
  * come before any stream capture on that device.  Every call uses the same
  * array and leaves its contents behind: calls whose GPU work can overlap (on
  * different streams or from different host threads) race and must be
- * serialised by the caller.
+ * serialised by the caller.  Launch failures are returned directly; a
+ * failure inside the solve (info.status) is only seen when `info` is given,
+ * since only then does the call wait for the GPU.
  */
 int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int64_t* dims, int R,
                           const cpd_options* opts, const float* W0, float* W_out,

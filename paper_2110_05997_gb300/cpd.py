@@ -49,7 +49,8 @@ class cpd_options(C.Structure):
                 ("cg_a", C.c_double), ("cg_b", C.c_double), ("mlsvd_tol", C.c_double),
                 ("st_mlsvd", C.c_int), ("compress", C.c_int), ("init", C.c_int),
                 ("gram_precision", C.c_int), ("refine_maxiter", C.c_int),
-                ("seed", C.c_uint64), ("block_threads", C.c_int)]
+                ("seed", C.c_uint64), ("block_threads", C.c_int), ("mu_min", C.c_double),
+                ("timeout_cycles", C.c_longlong)]
 
 
 class cpd_info(C.Structure):

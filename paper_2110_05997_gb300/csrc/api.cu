@@ -49,6 +49,14 @@ int validate_common(int L, const int64_t* dims, int R) {
   return CPD_OK;
 }
 
+// The single-CTA solver (dGN on T itself, compress = 0) indexes the tensor
+// with 32-bit integers: larger tensors are refused before anything is sized.
+bool uncompressed_fits(int L, const int64_t* dims) {
+  double N = 1.0;
+  for (int l = 0; l < L; ++l) N *= (double)dims[l];
+  return N <= (double)(0x7fffffff - 1024);
+}
+
 int validate_options(const cpd_options* o) {
   if (o == nullptr) return CPD_OK;
   if (o->maxiter < 1 || o->maxiter > 100000) return CPD_ERR_INVALID_ARG;
@@ -59,6 +67,7 @@ int validate_options(const cpd_options* o) {
   if (o->refine_maxiter < 0 || o->refine_maxiter > 100000) return CPD_ERR_INVALID_ARG;
   if (o->block_threads < 0 || o->block_threads > 1024 || (o->block_threads % 32) != 0)
     return CPD_ERR_INVALID_ARG;
+  if (!(o->mu_min >= 0.0) || o->timeout_cycles < 0) return CPD_ERR_INVALID_ARG;
   return CPD_OK;
 }
 
@@ -74,17 +83,6 @@ size_t smem_limit() {
       lim = 227 * 1024;
   }
   return lim;
-}
-
-// CTA size of the single-CTA solvers: one thread per unknown, rounded up to
-// whole warps (every per-entry phase of the CG then takes one pass; more
-// warps than that only add barrier cost), at least 4 warps, at most 1024.
-int threads_for(const cpd_options* o, int n) {
-  if (o && o->block_threads > 0) return o->block_threads;
-  int t = (n + 31) / 32 * 32;
-  if (t < 128) t = 128;
-  if (t > 1024) t = 1024;
-  return t;
 }
 
 // Everything the solve needs, carved from the workspace (or sized when base == nullptr).
@@ -289,7 +287,7 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
     a.s_f64 = dtype == CPD_F64;
   }
   a.seed = o.seed; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
-  a.maxiter = o.maxiter; a.mu0 = -1.0; a.k0 = 0;
+  a.maxiter = o.maxiter; a.mu0 = -1.0; a.mu_min = o.mu_min; a.k0 = 0;
   a.big_in_smem = p.big_in_smem; a.gscratch = p.gscratch;
   a.hist = p.hist; a.trace = trace; a.trace_cap = trace_cap; a.trace_slot0 = 0;
   a.W_out = p.W_core; a.res = p.res;
@@ -317,7 +315,7 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
     sa.L = L; sa.R = R; sa.W = Wr; sa.G = p.rG; sa.esq = p.resq; sa.state = p.rstate;
     for (int l = 0; l < CPD_MAX_ORDER; ++l) sa.dims[l] = p.dims[l];
     sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = o.refine_maxiter;
-    sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.seed = o.seed; sa.hist = p.rhist;
+    sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.mu_min = o.mu_min; sa.seed = o.seed; sa.hist = p.rhist;
     sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
     sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
     const int rthreads = 1024;
@@ -432,6 +430,8 @@ void cpd_default_options(cpd_options* o) {
   o->refine_maxiter = 0;
   o->seed = 0;
   o->block_threads = 0;
+  o->mu_min = 1e-5;
+  o->timeout_cycles = 0;
 }
 
 const char* cpd_status_string(int s) {
@@ -451,6 +451,7 @@ size_t cpd_workspace_size(int L, const int64_t* dims, int R, const cpd_options* 
   if (validate_common(L, dims, R) != CPD_OK) return 0;
   cpd_options o; cpd_default_options(&o);
   if (opts) o = *opts;
+  if (!o.compress && !uncompressed_fits(L, dims)) return 0;
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = CPD_F32;
   Carver c(nullptr, 0);
   plan_solve(p, c, o);
@@ -479,6 +480,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   if (o.gram_precision == CPD_GRAM_BF16 && !gram_bf16_tc_supported(dims[0], static_cast<const float*>(T)))
     return CPD_ERR_UNSUPPORTED;
   if (o.refine_maxiter > 0 && !pass_ok(L, dims, R)) return CPD_ERR_UNSUPPORTED;
+  if (!o.compress && !uncompressed_fits(L, dims)) return CPD_ERR_UNSUPPORTED;
 
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
   Carver c(workspace, ws_bytes);

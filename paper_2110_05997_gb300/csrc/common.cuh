@@ -105,15 +105,21 @@ __device__ inline void block_sum_f(const float (&in)[NV], float (&out)[NV], doub
   }
 }
 
-// a / b and sqrt(x) to ~FP64 accuracy from an FP32 estimate and one FP64
-// correction step (2-3 FP64 FMAs instead of a full FP64 division / square
-// root sequence).  Valid while a, b, x are within the FP32 exponent range.
-__device__ __forceinline__ double quick_div(double a, double b) {
+// a / b and sqrt(x) to ~FP64 accuracy from an FP32 estimate and one step of
+// Newton's method in FP64 (2-3 FP64 FMAs instead of a full FP64 division /
+// square root sequence).
+//   quotient: q1 = q0 + (a - q0 b) / b with the residual a - q0 b formed by one
+//     FMA and the division by b taken with the FP32 reciprocal; the relative
+//     error of q0 (~2^-22) is squared, giving ~2^-46;
+//   square root: s1 = s0 + (x - s0^2) / (2 s0), Newton's (Heron's) step for
+//     s^2 = x from the FP32 root s0, again squaring its relative error.
+// Valid while a, b, x and the results are within the FP32 exponent range.
+__host__ __device__ __forceinline__ double quick_div(double a, double b) {
   const float rb = 1.f / (float)b;
   const double q0 = (double)((float)a * rb);
   return fma(fma(-q0, b, a), (double)rb, q0);
 }
-__device__ __forceinline__ double quick_sqrt(double x) {
+__host__ __device__ __forceinline__ double quick_sqrt(double x) {
   if (!(x > 0.0)) return x == 0.0 ? 0.0 : sqrt(x);
   const float s0 = sqrtf((float)x);
   const double s = (double)s0;

@@ -196,7 +196,7 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
       step = quick_sqrt(step);
       double m = st.mu;
       const double Fn = 0.5 * fsq;
-      const double gain = gain_update(st.F, Fn, pred_drop, m);
+      const double gain = gain_update(st.F, Fn, pred_drop, m, a.mu_min);
       const double e = st.normS > 0.0 ? quick_div(quick_sqrt(fsq), st.normS) : 0.0;
       st.mu = m; st.F = Fn; st.rel_err = e; st.grad_inf = ginf;
       st.cg_total += its; st.iters = k; st.kglob = a.k0 + k;

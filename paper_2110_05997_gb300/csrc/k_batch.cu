@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(TH) k_batch(BatchArgs a, int dmax, int Rmax, s
       }
     }
     da.tol = a.tol; da.tau = a.tau; da.cg_a = a.cg_a; da.cg_b = a.cg_b; da.maxiter = a.maxiter;
-    da.mu0 = -1.0; da.k0 = 0; da.big_in_smem = 1; da.gscratch = nullptr;
+    da.mu0 = -1.0; da.mu_min = a.mu_min; da.k0 = 0; da.big_in_smem = 1; da.gscratch = nullptr;
     da.hist = hist; da.trace = nullptr; da.trace_cap = 0; da.trace_slot0 = 0;
     da.W_out = gs + lay.Wc; da.res = dres; da.cgtab = cgtab; da.cgtab_len = a.maxiter;
     __syncthreads();
@@ -744,7 +744,7 @@ int batch_ex(int mode, int B, const float* T_packed, const int64_t* t_off, const
   a.scratch = reinterpret_cast<float*>(ws + e.p.scratch);
   a.scratch_floats_per_cta = e.p.per_cta;
   a.hist = reinterpret_cast<double*>(ws + e.p.hist);
-  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
+  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b; a.mu_min = o.mu_min;
   a.mlsvd_tol = o.mlsvd_tol; a.compress = 1; a.seed = o.seed; a.ctas = e.p.ctas;
   a.store = reinterpret_cast<float*>(ws + e.store);
   a.store_floats = e.store_floats;
@@ -822,7 +822,7 @@ int cpd_batch_solve(int B, const float* T_packed, const int64_t* t_off, const in
   a.scratch = reinterpret_cast<float*>(ws + p.scratch);
   a.scratch_floats_per_cta = p.per_cta;
   a.hist = reinterpret_cast<double*>(ws + p.hist);
-  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
+  a.maxiter = o.maxiter; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b; a.mu_min = o.mu_min;
   a.mlsvd_tol = o.mlsvd_tol; a.compress = o.compress; a.init = o.init; a.seed = o.seed; a.ctas = p.ctas;
   auto direct = [&](int TH) -> int {
     if (cudaMemcpyAsync(ws + p.items, items.data(), sizeof(BatchItem) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)

@@ -75,6 +75,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   if (o.init == CPD_INIT_GIVEN && W0 == nullptr) return CPD_ERR_INVALID_ARG;
   if (o.block_threads < 0 || o.block_threads > 1024 || (o.block_threads % 32) != 0)
     return CPD_ERR_INVALID_ARG;
+  if (!(o.mu_min >= 0.0) || o.timeout_cycles < 0) return CPD_ERR_INVALID_ARG;
   int d[CPD_MAX_ORDER] = {1, 1, 1, 1};
   long long n = 0;
   double N = 1.0;
@@ -114,12 +115,12 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   a.S = T; a.s_f64 = (dtype == CPD_F64);
   a.W0 = W0; a.init = o.init; a.seed = o.seed;
   a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b; a.maxiter = o.maxiter;
-  a.mu0 = -1.0; a.k0 = 0;
+  a.mu0 = -1.0; a.mu_min = o.mu_min; a.k0 = 0;
   a.big_in_smem = 1; a.gscratch = nullptr;
   a.hist = hist; a.trace = nullptr; a.trace_cap = 0; a.trace_slot0 = 0;
   a.W_out = Wc; a.res = res;
   a.cgtab = cgtab; a.cgtab_len = o.maxiter;
-  const int threads = o.block_threads > 0 ? o.block_threads : (n > 2048 ? 1024 : 256);
+  const int threads = threads_for(&o, (int)n);   // the CTA size cpd_dgn_solve launches
   if (launch_dgn_core(L, a, threads, smem, st) != cudaSuccess) return CPD_ERR_CUDA;
   long long ld[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) ld[l] = dims[l];
@@ -135,5 +136,5 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
     info->grad_inf = hr.grad_inf;
     for (int l = 0; l < L; ++l) info->core_dims[l] = d[l];
   }
-  return cudaGetLastError() == cudaSuccess ? CPD_OK : CPD_ERR_CUDA;
+  return CPD_OK;      // every launch's own status was checked above
 }

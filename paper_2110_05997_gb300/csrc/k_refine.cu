@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
     } else {
       double mu = st->mu;
       const double Fn = 0.5 * esq;
-      const double gain = gain_update(st->F, Fn, st->pred_drop, mu);
+      const double gain = gain_update(st->F, Fn, st->pred_drop, mu, a.mu_min);
       const double e = st->normT > 0.0 ? quick_div(quick_sqrt(esq), st->normT) : 0.0;
       st->mu = mu; st->F = Fn; st->rel_err = e; st->iters = jr;
       a.hist[jr] = e;

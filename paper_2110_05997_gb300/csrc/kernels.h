@@ -37,6 +37,7 @@ struct DgnArgs {
   double tol, tau, cg_a, cg_b;
   int maxiter;
   double mu0;                 // < 0: tau * mean|S|
+  double mu_min;              // floor of mu after each update (0: none)
   int k0;                     // global iteration offset for cg_maxiter
   int big_in_smem;
   float* gscratch;            // tensor-sized buffers when not in shared memory
@@ -70,6 +71,17 @@ struct JtjArgs {
 };
 
 size_t dgn_smem_bytes_host(int L, const int* d, int R, int big_in_smem);
+
+// CTA size of the single-CTA solvers: one thread per unknown, rounded up to
+// whole warps (every per-entry phase of the CG then takes one pass; more
+// warps than that only add barrier cost), at least 4 warps, at most 1024.
+inline int threads_for(const cpd_options* o, int n) {
+  if (o && o->block_threads > 0) return o->block_threads;
+  int t = (n + 31) / 32 * 32;
+  if (t < 128) t = 128;
+  if (t > 1024) t = 1024;
+  return t;
+}
 size_t dgn_gscratch_floats_host(int L, const int* d, int R);
 
 cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st);
@@ -164,6 +176,7 @@ struct RefineStepArgs {
   int j;                      // refinement iteration index (0 = only prime the state)
   int maxiter;
   double tol, cg_a, cg_b;
+  double mu_min;              // floor of mu after each update (0: none)
   uint64_t seed;
   double* hist;               // maxiter + 1
   double* trace;
@@ -204,6 +217,7 @@ struct BatchArgs {
   double* hist;               // per-CTA history, maxiter + 1 each
   int maxiter;
   double tol, tau, cg_a, cg_b, mlsvd_tol;
+  double mu_min;              // floor of mu after each update (0: none)
   int compress, init;
   uint64_t seed;
   int ctas;

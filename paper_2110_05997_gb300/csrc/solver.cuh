@@ -569,11 +569,16 @@ __device__ inline void fill_cg_table(int* tab, int len, uint64_t seed, double ca
 }
 
 // Gain ratio (Sec. 3.5.2 / 4.1.3) and the damping update x3 below 0.25,
-// /3 above 0.75 (the rule Sec. 4.1.3 settles on).
-__device__ inline double gain_update(double F_old, double F_new, double pred_drop, double& mu) {
+// /3 above 0.75 (the rule Sec. 4.1.3 settles on), then the FP32 floor mu_min:
+// the CG runs in FP32, and with mu far below the FP32 unit roundoff the
+// rounding of J^T J v is amplified by ~1/mu along the scaling null space of
+// J^T J (Sec. 3.5, "J^T J is singular"), which can overflow the step.
+__device__ inline double gain_update(double F_old, double F_new, double pred_drop, double& mu,
+                                     double mu_min) {
   const double g = pred_drop > 0.0 ? quick_div(F_old - F_new, pred_drop) : 0.0;
   if (g < 0.25) mu *= 3.0;
   else if (g > 0.75) mu /= 3.0;
+  if (mu < mu_min) mu = mu_min;
   return g;
 }
 

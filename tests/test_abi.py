@@ -44,6 +44,8 @@ def test_defaults_are_the_thesis_defaults(cpd):
     assert o.maxiter == 200 and o.tol == 1e-6 and o.tau == 1.0
     assert o.cg_a == 0.4 and o.cg_b == 0.9
     assert o.st_mlsvd == 1 and o.compress == 1 and o.init == 0
+    # the FP32 damping floor (not in the thesis) and the default wait budget
+    assert o.mu_min == 1e-5 and o.timeout_cycles == 0
     assert cpd.cpd_status_string(-1) == "invalid argument"
 
 
@@ -103,6 +105,15 @@ def test_validation_before_launch(cpd):
     assert solve(3, (4, 4, 4), 2, opts=bad) == -1
     bad = cpd.cpd_default_options(block_threads=100)
     assert solve(3, (4, 4, 4), 2, opts=bad) == -1
+    bad = cpd.cpd_default_options(mu_min=-1.0)
+    assert solve(3, (4, 4, 4), 2, opts=bad) == -1
+    bad = cpd.cpd_default_options(timeout_cycles=-5)
+    assert solve(3, (4, 4, 4), 2, opts=bad) == -1
+    # dGN on T itself (one CTA, 32-bit entry indices) is refused beyond 2^31 - 1024
+    # entries, before anything is sized or launched
+    o_unc = cpd.cpd_default_options(compress=0)
+    assert solve(3, (1300, 1300, 1300), 5, opts=o_unc) == -6
+    assert cpd.cpd_workspace_size((1300, 1300, 1300), 5, o_unc) == 0
     # FP64 input only for the uncompressed path
     assert L.cpd_dgn_solve(dummy, 1, 3, cpd._dims((4, 4, 4)), 2, C.byref(o), nul, dummy, dummy,
                            C.byref(info), nul, dummy, 1 << 20, nul) == -6

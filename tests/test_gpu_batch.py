@@ -1,19 +1,22 @@
 """GPU parity of the batched solver (one persistent launch, one CTA per CPD)
 against the FP64 oracle run item by item with the same options and seeds.
 
-Parity is asserted where the method itself reaches the noise floor on the
-oracle's side (planted problems with the MLSVD-energy start occasionally
-stall in a local minimum; those items are counted and excluded, and most
-items must converge).  dGN converges to a local minimum (Sec. 3.5) and some
-starts lead into one (Sec. 4.1.2): starts that agree to FP32 rounding can
-end at different stationary points, so an item on which only the GPU run
-stalls is a trajectory split, not a parity failure; splits must be rare
-(at most 10% of the items the oracle solves) and end with a normal stop.  These workloads have noise 1e-6 = tol: the
-improvement stop test (|e_{k-1} - e_k| < tol) then fires at an iteration
-that depends on rounding, so FP32 and FP64 runs end a few iterations apart
-and their fits differ by up to a few tol.  The bar is therefore: a large
-majority of items within 1e-6 absolute of the oracle's fit (with factors
-within 1e-4 after alignment), and every converged item within 5e-6."""
+The bar, per item, with "solved" meaning a fit below 10x the noise level:
+  * an item both sides solve has |fit_GPU - fit_oracle| <= 1e-6 (both scored by
+    the oracle's FP64 evaluator) and factors within 1e-4 after alignment;
+  * dGN converges to a local minimum (Sec. 3.5) and some starts lead into one
+    (Sec. 4.1.2); starts that agree to FP32 rounding can end at different
+    stationary points, so an item can stall on one side only.  Items that stall
+    on the GPU only must be no more frequent than items that stall in the
+    oracle only (on the 1024-item sample; small cases allow one item of
+    sampling slack), and every item ends with a normal stop.
+These workloads have noise eta = 1e-6.  With the stop tolerance at the noise
+level (tol = 1e-6) the improvement test |e_{k-1} - e_k| < tol fires at an
+iteration that depends on rounding, above the noise floor, and 1 % of the
+items then differ from the oracle by up to 2e-6; the batched workload is
+therefore run with tol = 1e-7, one decade below the noise, on both sides."""
+import os
+
 import numpy as np
 import pytest
 
@@ -64,42 +67,49 @@ def run_batch(cpd, items, **kw):
     return [unpack(W, lam, w_off[b], l_off[b], dims[b], ranks[b]) for b in range(len(items))], infos
 
 
-def check_item(it, Wg, lg, seed, rel_eta):
-    """Returns None when the oracle stalls (not converged), "split" when only
-    the GPU run stalls, else True when the GPU result meets the 1e-6 fit bar
-    (factors then checked), False when it does not (but is within 5e-6)."""
+TOL = 1e-7
+
+
+def check_item(it, Wg, lg, seed, rel_eta, tol=TOL):
+    """"both" (after asserting the fit and factor bar) when both sides solve
+    the item, "oracle_only" / "gpu_only" when only that side stalls, None when
+    both stall."""
     T = it["T"].astype(np.float64)
-    Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=int(seed)))
+    Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=int(seed), tol=tol))
+    return judge(T, it["R"], Wg, lg, Wo, lo, rel_eta)
+
+
+def judge(T, R, Wg, lg, Wo, lo, rel_eta):
     fo, fg = O.fit(T, Wo, lo), O.fit(T, Wg, lg)
-    if fo >= 10 * rel_eta:
+    so, sg = fo >= 10 * rel_eta, fg >= 10 * rel_eta
+    if so and sg:
         return None
-    if fg >= 10 * rel_eta:
-        return "split"
-    assert abs(fg - fo) <= 5e-6, (fg, fo, it["T"].shape, it["R"])
-    if abs(fg - fo) > 1e-6:
-        return False
+    if so:
+        return "oracle_only"
+    if sg:
+        return "gpu_only"
+    assert abs(fg - fo) <= 1e-6, (fg, fo, T.shape, R)
     c = O.compare_cpd(Wg, lg, Wo, lo)
     assert max(c["mode_err"]) <= 1e-4 and c["lam_err"] <= 1e-4, c
-    return True
+    return "both"
 
 
-def summarize(results, min_converged, min_within, max_split=0.1):
-    conv = [r for r in results if r is not None]
-    assert len(conv) >= min_converged * len(results), (len(conv), len(results))
-    split = [r for r in conv if r == "split"]
-    assert len(split) <= max_split * len(conv), (len(split), len(conv))
-    both = [r for r in conv if r != "split"]
-    assert sum(both) >= min_within * len(both), (sum(both), len(both))
+def summarize(results, min_solved, slack=1):
+    n = len(results)
+    both = results.count("both")
+    go, oo = results.count("gpu_only"), results.count("oracle_only")
+    assert both >= min_solved * n, (both, n)
+    assert go <= oo + slack, (go, oo)
 
 
 def test_batch_small_uneven_matches_oracle(cpd):
     items = synth.c4_batch(seed=7, B=48, lo=6, hi=20, rlo=1, rhi=6, eta=1e-6)
-    res, infos = run_batch(cpd, items, seed=11)
+    res, infos = run_batch(cpd, items, seed=11, tol=TOL)
     out = []
     for b, (it, (Wg, lg)) in enumerate(zip(items, res)):
         assert infos[b]["status"] == 0
         out.append(check_item(it, Wg, lg, 11 + b, 1e-6))
-    summarize(out, 0.8, 0.85)
+    summarize(out, 0.75)
 
 
 def test_batch_equals_single_solves(cpd):
@@ -124,35 +134,50 @@ def test_batch_edge_shapes(cpd):
     for i, (dims, R) in enumerate(shapes):
         T, Wt = synth.planted(500 + i, dims, R, 0.0, 1e-6, np.float32)
         items.append(dict(T=T, R=R, W_true=Wt))
-    res, infos = run_batch(cpd, items, seed=1)
+    res, infos = run_batch(cpd, items, seed=1, tol=TOL)
     out = []
     for b, it in enumerate(items):
         assert infos[b]["status"] == 0
         out.append(check_item(it, *res[b], 1 + b, 1e-6))
-    summarize(out, 0.6, 0.6)
+    summarize(out, 0.6)
 
 
 def test_batch_uncompressed(cpd):
     items = synth.c4_batch(seed=9, B=8, lo=4, hi=9, rlo=1, rhi=3, eta=1e-6)
-    res, infos = run_batch(cpd, items, seed=2, compress=0)
+    res, infos = run_batch(cpd, items, seed=2, compress=0, tol=TOL)
+    out = []
     for b, it in enumerate(items):
+        assert infos[b]["status"] == 0
         T = it["T"].astype(np.float64)
-        Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=2 + b, compress=False))
-        fo, fg = O.fit(T, Wo, lo), O.fit(T, *res[b])
-        if fo < 1e-5:
-            assert abs(fg - fo) <= 1e-6
+        Wo, lo, io = O.cpd(T, it["R"], O.Options(seed=2 + b, compress=False, tol=TOL))
+        out.append(judge(T, it["R"], *res[b], Wo, lo, 1e-6))
+    summarize(out, 0.6)
+
+
+def _oracle_item(args):
+    import oracle as Ow
+    T, R, seed, tol = args
+    T = T.astype(np.float64)
+    Wo, lo, _ = Ow.cpd(T, R, Ow.Options(seed=int(seed), tol=tol))
+    return Wo, lo
 
 
 def test_batch_full_4096_sampled_parity(cpd):
     """The uneven-batch workload: 4096 FP32 tensors, modes U{8..48}, ranks U{2..8},
-    noise 1e-6; every item solved, a seeded sample checked against the oracle."""
+    noise 1e-6; every item solved on the GPU, a seeded sample of 1024 items
+    solved by the oracle (a pool of spawned processes) and held to the bar."""
+    import multiprocessing as mp
     items = synth.c4_batch()
-    res, infos = run_batch(cpd, items, seed=0)
+    pick = np.random.default_rng(99).choice(len(items), size=1024, replace=False)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ref = pool.map(_oracle_item, [(items[b]["T"], items[b]["R"], int(b), TOL) for b in pick], chunksize=8)
+    res, infos = run_batch(cpd, items, seed=0, tol=TOL)
     assert all(inf["status"] == 0 for inf in infos)
     assert all(1 <= inf["stop"] <= 8 for inf in infos)
-    pick = np.random.default_rng(123).choice(len(items), size=32, replace=False)
-    out = [check_item(items[int(b)], *res[int(b)], int(b), 1e-6) for b in pick]
-    summarize(out, 0.75, 0.85)
+    out = [judge(items[int(b)]["T"].astype(np.float64), items[int(b)]["R"], *res[int(b)], Wo, lo, 1e-6)
+           for b, (Wo, lo) in zip(pick, ref)]
+    print({k: out.count(k) for k in ("both", "oracle_only", "gpu_only", None)})
+    summarize(out, 0.75, slack=0)
 
 
 def test_batch_graph_replay_and_cta_sizes(cpd):
@@ -169,21 +194,21 @@ def test_batch_graph_replay_and_cta_sizes(cpd):
     outs = []
     for _ in range(3):
         with torch.cuda.stream(st):
-            W, lam, w_off, l_off, infos = cpd.cpd_batch_solve(Tp, offs, dims, ranks, cpd.cpd_default_options(seed=5),
-                                                              stream=st)
+            W, lam, w_off, l_off, infos = cpd.cpd_batch_solve(Tp, offs, dims, ranks,
+                                                              cpd.cpd_default_options(seed=5, tol=TOL), stream=st)
         torch.cuda.synchronize()
         outs.append((W.clone(), lam.clone()))
     assert all(torch.equal(outs[0][0], o[0]) and torch.equal(outs[0][1], o[1]) for o in outs[1:])
     fits = {}
     for th in (64, 128, 256):
-        res, inf = run_batch(cpd, items, seed=5, block_threads=th)
+        res, inf = run_batch(cpd, items, seed=5, block_threads=th, tol=TOL)
         assert all(i["status"] == 0 for i in inf)
         fits[th] = [O.fit(it["T"].astype(np.float64), *res[b]) for b, it in enumerate(items)]
     split = 0
     for b in range(len(items)):
         f = [fits[th][b] for th in (64, 128, 256)]
         if max(f) < 1e-5:
-            assert max(f) - min(f) <= 5e-6, f
+            assert max(f) - min(f) <= 1e-6, f
         elif min(f) < 1e-5:
             split += 1  # one Gram summation order stalls where another converges
     assert split <= 0.1 * len(items), split

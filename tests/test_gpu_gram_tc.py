@@ -84,7 +84,7 @@ def test_bf16_compressed_refined_solve_matches_oracle(cpd, seed, dims, R, rho, e
     fg, fo = O.fit(T64, Wg, lg), O.fit(T64, Wo, lo)
     assert abs(fg - fo) <= 1e-6, (fg, fo, info)
     c = O.compare_cpd(Wg, lg, Wo, lo)
-    assert max(c["mode_err"]) <= 1e-3 and c["lam_err"] <= 1e-3, c
+    assert max(c["mode_err"]) <= 1e-4 and c["lam_err"] <= 1e-4, c
 
 
 def test_bf16_full_size_workload_matches_oracle(cpd):
@@ -102,3 +102,5 @@ def test_bf16_full_size_workload_matches_oracle(cpd):
     Wo, lo, io = O.cpd(T64, R, O.Options(refine_maxiter=20))
     fg, fo = O.fit(T64, Wg, lg), O.fit(T64, Wo, lo)
     assert abs(fg - fo) <= 1e-6, (fg, fo, info)
+    c = O.compare_cpd(Wg, lg, Wo, lo)
+    assert max(c["mode_err"]) <= 1e-4 and c["lam_err"] <= 1e-4, c

@@ -5,11 +5,12 @@ refinement on the full tensor, against the FP64 oracle on the same input.
 
 The start is random (the same SplitMix64 Box-Muller draws on both sides,
 Sec. 4.1.2): on this order-4, rank-15 problem the MLSVD-energy start stalls
-in a local minimum (fit ~0.2) on both sides, so the random start is the one
-the method is run with here, with a seed whose start converges (with other
-seeds the random start can stall too; a stalled FP32 trajectory, whose
-damping parameter falls to ~1e-8, can then overflow where the FP64 oracle
-only stalls)."""
+in a local minimum (relative error ~0.3-0.46) on both sides.  Every random
+seed on which the FP64 oracle reaches the noise floor (0, 1, 2, 4 of 0..7) is
+checked; on seeds 3, 5, 6 the oracle stalls and on 7 it diverges (its damping
+parameter falls to ~1e-55), so those seeds carry no parity claim.  The FP32
+solver's damping floor (cpd_options.mu_min) keeps its CG well conditioned;
+without it seeds 1, 2 and 3 overflowed to NaN on the GPU."""
 import time
 
 import numpy as np
@@ -33,12 +34,12 @@ def cpd():
     return m
 
 
-@pytest.mark.parametrize("gram", ["bf16", "fp32"])
-def test_order4_full_size_matches_oracle(cpd, gram):
+@pytest.mark.parametrize("gram,seed", [("bf16", 0), ("bf16", 1), ("bf16", 2), ("bf16", 4), ("fp32", 0)])
+def test_order4_full_size_matches_oracle(cpd, gram, seed):
     c = synth.c3_order4()
     T, R = c["T"], c["R"]
     Td = torch.from_numpy(synth.flat(T)).cuda()
-    opts = cpd.cpd_default_options(init="random", gram_precision=gram, refine_maxiter=5, seed=0)
+    opts = cpd.cpd_default_options(init="random", gram_precision=gram, refine_maxiter=20, seed=seed)
     W, lam, info, _ = cpd.cpd_dgn_solve(Td, T.shape, R, opts)            # warm-up (graph capture)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -50,11 +51,27 @@ def test_order4_full_size_matches_oracle(cpd, gram):
     T64 = T.astype(np.float64)
     Wg = [w.double().cpu().numpy() for w in W]
     lg = lam.double().cpu().numpy()
-    Wo, lo, io = O.cpd(T64, R, O.Options(init="random", refine_maxiter=5, seed=0))
+    Wo, lo, io = O.cpd(T64, R, O.Options(init="random", refine_maxiter=20, seed=seed))
     fg, fo = O.fit(T64, Wg, lg), O.fit(T64, Wo, lo)
-    print(f"order-4 {gram}: GPU solve {dt * 1e3:.1f} ms, core {info['core_dims']}, iters {info['iters']}, "
-          f"refine {info['refine_iters']}; fit GPU {fg:.9e} oracle {fo:.9e}")
+    print(f"order-4 {gram} seed {seed}: GPU solve {dt * 1e3:.1f} ms, core {info['core_dims']}, "
+          f"iters {info['iters']}, refine {info['refine_iters']}; fit GPU {fg:.9e} oracle {fo:.9e}")
     assert fo < 2e-5                              # the oracle reaches the noise floor
     assert abs(fg - fo) <= 1e-6, (fg, fo, info)
     cmp = O.compare_cpd(Wg, lg, Wo, lo)
     assert max(cmp["mode_err"]) <= 1e-4 and cmp["lam_err"] <= 1e-4, cmp
+
+
+def test_order4_stalled_starts_end_finite(cpd):
+    """Starts on which the FP64 oracle stalls (seed 5, and the MLSVD-energy
+    start) end with a normal stop and finite factors on the GPU, not with an
+    overflow."""
+    c = synth.c3_order4()
+    T, R = c["T"], c["R"]
+    Td = torch.from_numpy(synth.flat(T)).cuda()
+    for init, seed in (("random", 5), ("mlsvd", 0)):
+        opts = cpd.cpd_default_options(init=init, gram_precision="bf16", refine_maxiter=20, seed=seed)
+        W, lam, info, _ = cpd.cpd_dgn_solve(Td, T.shape, R, opts)
+        torch.cuda.synchronize()
+        assert info["status"] == 0 and 1 <= info["stop"] <= 8, info
+        assert all(bool(torch.isfinite(w).all()) for w in W) and bool(torch.isfinite(lam).all())
+        assert info["refine_rel_err"] < 1.0, info
