@@ -24,7 +24,8 @@ from .mlsvd import (gram_left_singular, mlsvd_classic, mlsvd_st, truncation_rank
 from .dgn import (Options, splitmix64, cg_maxiter, residual, neg_gradient, grams,
                   pi_matrices, jtj_apply, regularizer, preconditioner, pcg, balance,
                   init_mlsvd_energy, init_random, dgn, uncompress, normalize, cpd,
-                  window_constant, gain_ratio, update_mu, stop_reason, STOP_NAMES)
+                  window_constant, gain_ratio, update_mu, stop_reason, block_preconditioner, pcg_block,
+                  STOP_NAMES)
 from .evaluate import fit, align, compare_cpd
 
 __all__ = [n for n in dir() if not n.startswith("_")]

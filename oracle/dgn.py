@@ -68,6 +68,8 @@ class Options:
     init: str = "mlsvd"         # "mlsvd" (Sec. 4.1.2 second approach), "random", "given"
     refine_maxiter: int = 0     # dGN iterations in the original space after uncompression
     seed: int = 0
+    precond: str = "jacobi"     # "jacobi": diagonal M (Sec. 4.8); "block": the exact
+                                # diagonal blocks of J^T J + mu D (Sec. 3.5.3 corollary)
 
 
 # --- SplitMix64 (Steele, Lea & Flood 2014) -----------------------------------
@@ -188,6 +190,58 @@ def preconditioner(Ws, gamma, mu: float):
                 p = p * nr[j] ** 2
         out.append(p + mu * gamma[l])
     return out
+
+
+def block_preconditioner(Pi1, gamma, mu: float):
+    """Block-Jacobi preconditioner: the diagonal blocks of J^T J + mu D.  By the
+    theorem on J^T J (Sec. 3.5.3) the block of mode l is Pi^(l) (x) I_{I_l}, and
+    D's block is diag(gamma^(l)) (x) I, so the block of mode l acts on vec(V^(l))
+    as V^(l) -> V^(l) (Pi^(l) + mu diag(gamma^(l))); returns the R x R matrices
+    B_l = Pi^(l) + mu diag(gamma^(l)) and their Cholesky factors."""
+    Bs = [P + mu * np.diag(g) for P, g in zip(Pi1, gamma)]
+    return Bs, [np.linalg.cholesky(B) for B in Bs]
+
+
+def pcg_block(Ws, Pi1, Pi2, g, gamma, chol, mu: float, maxit: int, tol: float):
+    """Preconditioned CG (App. A) on (J^T J + mu D) x = A^T b with the
+    block-Jacobi preconditioner: z = M^{-1} r is, per mode, the solve
+    Z^(l) B_l = R^(l) by the Cholesky factor of B_l.  The stop test is the
+    split form's ||M^{-1/2} r||^2 = r^T M^{-1} r < tol; returns (x, iterations)."""
+    def apply_A(P):
+        H = jtj_apply(Ws, Pi1, Pi2, P)
+        return [H[l] + mu * gamma[l][None, :] * P[l] for l in range(len(P))]
+
+    def precond(Rm):
+        out = []
+        for l, C in enumerate(chol):
+            # Z B = R with B = C C^T:  Z = R C^{-T} C^{-1}
+            Y = np.linalg.solve(C, Rm[l].T)          # C Y = R^T
+            out.append(np.linalg.solve(C.T, Y).T)    # C^T Z^T = Y
+        return out
+
+    x = [np.zeros_like(v) for v in g]
+    r = [v.copy() for v in g]
+    z = precond(r)
+    p = [v.copy() for v in z]
+    rz = _dot(r, z)
+    its = 0
+    for i in range(maxit):
+        q = apply_A(p)
+        pq = _dot(p, q)
+        if pq <= 0.0:
+            break
+        alpha = rz / pq
+        x = [xi + alpha * pi for xi, pi in zip(x, p)]
+        r = [ri - alpha * qi for ri, qi in zip(r, q)]
+        z = precond(r)
+        rz_new = _dot(r, z)
+        beta = rz_new / rz if rz > 0 else 0.0
+        p = [zi + beta * pi for zi, pi in zip(z, p)]
+        rz = rz_new
+        its = i + 1
+        if rz_new < tol:
+            break
+    return x, its
 
 
 def _dot(A, B) -> float:
@@ -367,9 +421,13 @@ def dgn(T: np.ndarray, W0, opts: Options, mu0: float | None = None, k0: int = 0,
         gr = grams(Ws)
         Pi1, Pi2 = pi_matrices(gr)
         gamma = regularizer(Ws)
-        Mdiag = preconditioner(Ws, gamma, mu)
         maxit = cg_maxiter(k0 + k, opts.seed, opts.cg_a, opts.cg_b)
-        x, its = pcg(Ws, Pi1, Pi2, g, gamma, Mdiag, mu, maxit, tol)
+        if opts.precond == "block":
+            _, chol = block_preconditioner(Pi1, gamma, mu)
+            x, its = pcg_block(Ws, Pi1, Pi2, g, gamma, chol, mu, maxit, tol)
+        else:
+            Mdiag = preconditioner(Ws, gamma, mu)
+            x, its = pcg(Ws, Pi1, Pi2, g, gamma, Mdiag, mu, maxit, tol)
         cg_total += its
         Hx = jtj_apply(Ws, Pi1, Pi2, x)
         pred_drop = _dot(g, x) - 0.5 * _dot(x, Hx)     # F - ½||f + Jx||^2
