@@ -53,6 +53,8 @@ struct TcArgs {
   int nk_full, nk;      // full steps, all steps (a ragged tail step last)
   int vec4;             // G rows may be added as float4
   unsigned tmem_cols;
+  int* err;             // set to CPD_ERR_TIMEOUT when a pipeline wait runs out (or nullptr)
+  long long budget;     // bound of every pipeline wait in SM clock cycles
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
     const int s = j % S, b = j & 1;
     const bool tail = k >= a.nk_full;
     bool fail = false;
-    if (!tail) fail = !mbar_wait(bar_full + 8u * s, (uint32_t)((j / S) & 1));
-    if (!fail && j >= 2) fail = !mbar_wait(bar_mma + 8u * b, (uint32_t)(((j - 2) >> 1) & 1));
+    if (!tail) fail = !mbar_wait_cycles(bar_full + 8u * s, (uint32_t)((j / S) & 1), a.budget);
+    if (!fail && j >= 2) fail = !mbar_wait_cycles(bar_mma + 8u * b, (uint32_t)(((j - 2) >> 1) & 1), a.budget);
     if (__syncthreads_or(fail)) { ok = false; break; }
     // FP32 stage -> BF16, K-major, 128-byte swizzle: element (i, kk) of the
     // step sits at (i/8)*1024 + (i%8)*128 + (((kk/8) ^ (i%8)) * 16) + (kk%8)*2.
@@ -205,13 +207,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
   }
   if (ok && nsteps > 0) {
     const int jl = nsteps - 1;
-    const bool fail = !mbar_wait(bar_mma + 8u * (jl & 1), (uint32_t)((jl >> 1) & 1));
+    const bool fail = !mbar_wait_cycles(bar_mma + 8u * (jl & 1), (uint32_t)((jl >> 1) & 1), a.budget);
     if (__syncthreads_or(fail)) ok = false;
   }
   const bool has_d = ok && nsteps > 0;             // this CTA holds a valid partial D
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!ok && tid == kIssuer) {
-    a.G[0] = __int_as_float(0x7fc00000);           // NaN: the solve reports a numeric failure
+    a.G[0] = __int_as_float(0x7fc00000);           // NaN: the eigen-solve cannot use G
+    if (a.err) atomicExch(a.err, CPD_ERR_TIMEOUT);   // the solve reports the timeout
     // bounded waits for this CTA's copies and MMAs still in flight
     for (int j = done; j < issued; ++j) (void)mbar_wait(bar_full + 8u * (uint32_t)(j % S), (uint32_t)((j / S) & 1));
     if (committed > 0) {
@@ -352,10 +355,12 @@ bool gram_bf16_tc_supported(long long I, const float* T) {
 }
 
 cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float* G, float* scratch,
-                                size_t scratch_bytes, cudaStream_t st) {
+                                size_t scratch_bytes, cudaStream_t st, int* err, long long budget) {
   (void)scratch; (void)scratch_bytes;
   if (!gram_bf16_tc_supported(I, T) || C < 1) return cudaErrorNotSupported;
   TcArgs a{};
+  a.err = err;
+  a.budget = budget > 0 ? budget : (1ll << 31);
   a.A = T; a.G = G; a.C = C; a.I = (int)I;
   a.nM = I > 128 ? 2 : 1;
   a.N = (int)((I + 15) / 16 * 16);

@@ -41,6 +41,7 @@ cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st) {
   if (!refine_pass_supported(a.L, a.dims, a.R)) return cudaErrorInvalidValue;
   k_zero_pass<<<16, 256, 0, st>>>(a.G, n, a.esq, a.want_tsq, a.done);
   count_launch();
+  if (!a.cuda_cores && refine_tc_supported(a.L, a.dims, a.R, a.T)) return launch_refine_tc(a, st);
   const size_t smem = pass_smem(a.L, a.dims, a.R);
   long long nf = 1;
   for (int l = 1; l < a.L; ++l) nf *= a.dims[l];
@@ -50,12 +51,11 @@ cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st) {
 }
 
 // ---- the single-CTA step ----------------------------------------------------------
-size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem) {
+size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem, int blk) {
   size_t n = 0;
   for (int l = 0; l < L; ++l) n += (size_t)dims[l] * R;
-  const size_t RR = (size_t)R * R;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
-  size_t f = up(L * RR) + up((size_t)L * L * RR) + 2 * up(L * RR) + 3 * up((size_t)L * R);
+  size_t f = small_buf_floats(L, R, blk);
   if (vec_in_smem) f += 7 * up(n);
   return 128 * sizeof(double) + f * sizeof(float);
 }
@@ -84,18 +84,10 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   __syncthreads();
   const int jr = s_j;                          // this step's refinement iteration
   const int R = a.R;
-  const size_t RR = (size_t)R * R;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
   Bufs b{};
   b.red = reinterpret_cast<double*>(smem_raw);
-  float* p = reinterpret_cast<float*>(smem_raw + 128 * sizeof(double));
-  b.gram = p; p += up(L * RR);
-  b.Pi2 = p; p += up((size_t)L * L * RR);
-  b.Xm = p; p += up(L * RR);
-  b.Ym = p; p += up(L * RR);
-  b.msq = p; p += up((size_t)L * R);
-  b.gam = p; p += up((size_t)L * R);
-  b.sc = p; p += up((size_t)L * R);
+  float* p = carve_small(b, reinterpret_cast<float*>(smem_raw + 128 * sizeof(double)), L, R, a.precond);
   float* vb = a.vec_in_smem ? p : a.vecs;
   float** vecs[7] = {&b.W, &b.G, &b.X, &b.Rr, &b.P, &b.Z, &b.Tmp};
   for (int v = 0; v < 7; ++v) { *vecs[v] = vb; vb += up((size_t)s.n); }
@@ -107,7 +99,10 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   if (threadIdx.x == 0) {
     s_stop = 0;
     const double esq = a.esq[0];
-    if (jr > a.maxiter) {                       // not reached: the loop condition ends at maxiter
+    if (a.err && *a.err) {                      // the pass's bounded wait ran out: its sums are partial
+      st->status = CPD_ERR_TIMEOUT;
+      s_stop = 1;
+    } else if (jr > a.maxiter) {                       // not reached: the loop condition ends at maxiter
       if (st->stop == CPD_STOP_NONE) st->stop = CPD_STOP_MAXITER;
       s_stop = 1;
     } else if (jr == 0) {
@@ -146,10 +141,12 @@ __global__ void __launch_bounds__(1024) k_refine_step(RefineStepArgs a) {
   if (threadIdx.x == 0)
     s_maxit = (kglob <= a.cgtab_len) ? a.cgtab[kglob] : cg_maxiter(kglob, a.seed, a.cg_a, a.cg_b);
   grams_pi<L>(s, b);                           // its first barrier publishes s_maxit
-  regularize<L>(s, b, mu);
+  if (a.precond) regularize_block<L>(s, b, mu);
+  else regularize<L>(s, b, mu);
   const int maxit = s_maxit;
   int its;
-  if constexpr (RP > 0) its = pcg_rows<L, RP>(s, b, mu, maxit, a.tol);
+  if (a.precond) its = pcg_block<L>(s, b, mu, maxit, a.tol);
+  else if constexpr (RP > 0) its = pcg_rows<L, RP>(s, b, mu, maxit, a.tol);
   else its = pcg<L>(s, b, mu, maxit, a.tol);
   double pred_drop, step;
   finish_step<L>(s, b, pred_drop, step);
@@ -207,6 +204,90 @@ cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, 
   *status = h.status;
   if (steps_run) *steps_run = h.jnext;
   return cudaSuccess;
+}
+
+}  // namespace cpdk
+
+// ---- dGN on a large tensor without compression: every iteration a pass ----------
+namespace cpdk {
+
+__global__ void k_abs_sum(const float* T, long long N, double* out) {
+  float acc = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+    acc += fabsf(T[e]);
+  __shared__ double red[32];
+  double d = (double)acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    d = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (threadIdx.x == 0) atomicAdd(out, d);
+  }
+}
+
+// The starting factors on the full tensor (Sec. 4.1.2: random N(0,1) draws of
+// the same SplitMix64 stream as the core solver, or the caller's), balanced
+// (Sec. 4.1.3 "Updates"), and mu0 = tau mean|T| (Sec. 4.1.3) into the record
+// the refinement state is primed from.
+__global__ void __launch_bounds__(1024) k_full_start(int L, Dims4 dims, int R, int init, const float* W0,
+                                                     uint64_t seed, double tau, const double* abs_sum, float* W,
+                                                     DevResult* res) {
+  long long off[CPD_MAX_ORDER + 1];
+  off[0] = 0;
+  long long N = 1;
+  for (int l = 0; l < L; ++l) { off[l + 1] = off[l] + dims.v[l] * R; N *= dims.v[l]; }
+  const long long n = off[L];
+  for (long long j = threadIdx.x; j < n; j += blockDim.x)
+    W[j] = init == CPD_INIT_GIVEN ? W0[j] : (float)normal_draw(seed, (uint64_t)j);
+  __syncthreads();
+  __shared__ float nrm[CPD_MAX_ORDER * CPD_MAX_RANK];
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    const float* w = W + off[l] + (long long)r * dims.v[l];
+    float acc = 0.f;
+    for (long long i = 0; i < dims.v[l]; ++i) acc = fmaf(w[i], w[i], acc);
+    nrm[q] = sqrtf(acc);
+  }
+  __syncthreads();
+  __shared__ float scl[CPD_MAX_ORDER * CPD_MAX_RANK];
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    float lg = 0.f;
+    bool ok = true;
+    for (int j = 0; j < L; ++j) { const float v = nrm[j * R + r]; ok = ok && v > 0.f; lg += ok ? logf(v) : 0.f; }
+    scl[q] = ok ? expf(lg / L) / nrm[q] : 1.f;
+  }
+  __syncthreads();
+  for (int l = 0; l < L; ++l)
+    for (long long j = threadIdx.x; j < dims.v[l] * R; j += blockDim.x) W[off[l] + j] *= scl[l * R + j / dims.v[l]];
+  if (threadIdx.x == 0) {
+    res->status = CPD_OK; res->iters = 0; res->stop = 0; res->cg_total = 0; res->kglob = 0; res->pad0 = 0;
+    res->mu = tau * (*abs_sum) / (double)N;
+    res->rel_err = 0.0; res->grad_inf = 0.0; res->normS = 0.0;
+  }
+}
+
+cudaError_t launch_full_start(int L, const long long* dims, int R, int init, const float* W0, uint64_t seed,
+                              double tau, const float* T, double* abs_sum, float* W, DevResult* res,
+                              cudaStream_t st) {
+  long long N = 1;
+  Dims4 d{};
+  for (int l = 0; l < CPD_MAX_ORDER; ++l) d.v[l] = l < L ? dims[l] : 1;
+  for (int l = 0; l < L; ++l) N *= dims[l];
+  cudaError_t e = cudaMemsetAsync(abs_sum, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_abs_sum<<<4 * sms, 512, 0, st>>>(T, N, abs_sum);
+  count_launch();
+  k_full_start<<<1, 1024, 0, st>>>(L, d, R, init, W0, seed, tau, abs_sum, W, res);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace cpdk

@@ -38,6 +38,7 @@ struct DgnArgs {
   int maxiter;
   double mu0;                 // < 0: tau * mean|S|
   double mu_min;              // floor of mu after each update (0: none)
+  int precond;                // 0: diagonal (Jacobi) preconditioner; 1: block-Jacobi
   int k0;                     // global iteration offset for cg_maxiter
   int big_in_smem;
   float* gscratch;            // tensor-sized buffers when not in shared memory
@@ -70,7 +71,7 @@ struct JtjArgs {
   float* out;
 };
 
-size_t dgn_smem_bytes_host(int L, const int* d, int R, int big_in_smem);
+size_t dgn_smem_bytes_host(int L, const int* d, int R, int big_in_smem, int blk = 0);
 
 // CTA size of the single-CTA solvers: one thread per unknown, rounded up to
 // whole warps (every per-entry phase of the CG then takes one pass; more
@@ -85,6 +86,10 @@ inline int threads_for(const cpd_options* o, int n) {
 size_t dgn_gscratch_floats_host(int L, const int* d, int R);
 
 cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st);
+// The same solve by a cluster of csize CTAs (k_dgn_cluster.cu) for cores too
+// large for one CTA's shared memory: FP32 tensor, each CTA a slice of fibres.
+size_t dgn_cluster_smem_bytes_host(int L, const int* d, int R, int csize, int blk = 0);
+cudaError_t launch_dgn_cluster(int L, const DgnArgs& a, int threads, int csize, size_t smem, cudaStream_t st);
 cudaError_t launch_core_eval(int L, const CoreEvalArgs& a, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_jtj_apply(int L, const JtjArgs& a, int threads, size_t smem, cudaStream_t st);
 
@@ -99,8 +104,9 @@ struct View3 {
 };
 
 cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G, cudaStream_t st);
+// err / budget: see RefinePassArgs (a pipeline wait that runs out sets *err)
 cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float* G, float* scratch,
-                                size_t scratch_bytes, cudaStream_t st);
+                                size_t scratch_bytes, cudaStream_t st, int* err = nullptr, long long budget = 0);
 size_t gram_bf16_tc_scratch_bytes(long long I, long long C);
 bool gram_bf16_tc_supported(long long I, const float* T);
 // D(m, n) = epilogue(sum_k A(m, k) B(n, k)) on BF16 tensor cores (FP32 operands
@@ -160,9 +166,16 @@ struct RefinePassArgs {
   double* esq;                // [0] = ||e||^2, [1] = ||T||^2 (if want_tsq)
   int want_tsq;
   const int* done;            // skip when *done != 0 (refinement stopped)
+  int* err;                   // set to CPD_ERR_TIMEOUT by a bounded wait that ran out (or nullptr)
+  long long budget;           // bound of every wait in SM clock cycles (0 = default)
+  int cuda_cores;             // 1: force the CUDA-core pass
 };
 cudaError_t launch_refine_pass(const RefinePassArgs& a, cudaStream_t st);
 bool refine_pass_supported(int L, const long long* dims, int R);
+// the tensor-core pass (k_refine_tc.cu): R <= 16, I1 % 4 == 0, I1 <= 256,
+// T 16-byte aligned, fewer than 2^31 fibres, its shared memory within 227 KB
+bool refine_tc_supported(int L, const long long* dims, int R, const float* T);
+cudaError_t launch_refine_tc(const RefinePassArgs& a, cudaStream_t st);
 
 struct RefineStepArgs {
   int L, R;
@@ -187,11 +200,19 @@ struct RefineStepArgs {
   int j_from_state;           // 1: j is the state's iteration counter (a graph loop body)
   int use_cond;               // 1: set `cond` to 1 when another iteration follows, else 0
   cudaGraphConditionalHandle cond;
+  const int* err;             // nonzero: a bounded wait of the pass ran out; the refinement stops
+  int precond;                // 0: diagonal (Jacobi) preconditioner; 1: block-Jacobi
 };
-size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem);
+size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_smem, int blk = 0);
 cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, int* done,
                                cudaStream_t st);
+// dGN on a large tensor without compression (every iteration a pass over T):
+// the balanced starting factors on T (random or given) into W and mu0 =
+// tau mean|T| into *res, from which launch_refine_init primes the state.
+cudaError_t launch_full_start(int L, const long long* dims, int R, int init, const float* W0, uint64_t seed,
+                              double tau, const float* T, double* abs_sum, float* W, DevResult* res,
+                              cudaStream_t st);
 size_t refine_state_bytes();
 cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, int* cg_total,
                                double* rel_err, double* mu, int* status, int* steps_run, cudaStream_t st);

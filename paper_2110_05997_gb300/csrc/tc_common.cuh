@@ -32,6 +32,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// As mbar_try, but a thread whose phase is not yet complete may be suspended
+// for up to `hint_ns` nanoseconds (it resumes as soon as the phase completes),
+// so that a waiting warp does not take issue slots from the working ones.
+__device__ __forceinline__ bool mbar_try_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Poll the phase `parity` of the mbarrier at shared address `bar` at most
 // `limit` times; false when the phase did not complete within the budget.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
@@ -39,6 +54,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   for (long long it = 0; it < limit; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
+}
+
+// Poll the phase `parity` until it completes or `budget` SM clock cycles pass.
+__device__ __forceinline__ bool mbar_wait_cycles(uint32_t bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (clock64() - t0 > budget) return false;
+  }
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -117,6 +141,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
                : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
