@@ -82,6 +82,16 @@ typedef enum {
                            accuracy is won back by refinement in the original space */
 } cpd_gram_precision;
 
+/* Preconditioner of the CG inside each dGN iteration. */
+typedef enum {
+  CPD_PRECOND_JACOBI = 0,  /* the diagonal M of Sec. 4.8 (the thesis's choice)              */
+  CPD_PRECOND_BLOCK = 1    /* block-Jacobi: the exact diagonal blocks (Pi^(l) + mu diag
+                              gamma^(l)) (x) I of J^T J + mu D (Sec. 3.5.3, corollary on the
+                              diagonal blocks), inverted per mode by an FP64 R x R Cholesky
+                              factorisation; R <= 32, else CPD_ERR_UNSUPPORTED.  The batched
+                              solver always uses the diagonal one. */
+} cpd_precond;
+
 /* Element type of the input tensor. */
 typedef enum { CPD_F32 = 0, CPD_F64 = 1 } cpd_dtype;
 
@@ -111,6 +121,7 @@ typedef struct {
                            the tensor-core kernels, in SM clock cycles (0 = the
                            default of 2^31 cycles, about one second); a wait that
                            runs out ends the call with CPD_ERR_TIMEOUT */
+  int precond;          /* cpd_precond: CPD_PRECOND_JACOBI                        */
 } cpd_options;
 
 /* Outcome of one CPD. */

@@ -27,6 +27,7 @@ STOP = {0: "none", 1: "rel_err", 2: "step", 3: "improvement", 4: "grad", 5: "avg
 INIT = {"mlsvd": 0, "random": 1, "given": 2, "learned": 3}
 INITNET_CORE, INITNET_RANK, INITNET_IN, INITNET_IN_PAD, INITNET_HIDDEN, INITNET_OUT = 16, 8, 4104, 4160, 512, 384
 GRAM = {"fp32": 0, "bf16": 1}
+PRECOND = {"jacobi": 0, "block": 1}
 F32, F64 = 0, 1
 
 EXPORTS = ["cpd_default_options", "cpd_status_string", "cpd_workspace_size", "cpd_compress",
@@ -50,7 +51,7 @@ class cpd_options(C.Structure):
                 ("st_mlsvd", C.c_int), ("compress", C.c_int), ("init", C.c_int),
                 ("gram_precision", C.c_int), ("refine_maxiter", C.c_int),
                 ("seed", C.c_uint64), ("block_threads", C.c_int), ("mu_min", C.c_double),
-                ("timeout_cycles", C.c_longlong)]
+                ("timeout_cycles", C.c_longlong), ("precond", C.c_int)]
 
 
 class cpd_info(C.Structure):
@@ -167,6 +168,8 @@ def cpd_default_options(**kw) -> cpd_options:
             v = INIT[v]
         if k == "gram_precision" and isinstance(v, str):
             v = GRAM[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
         setattr(o, k, int(v) if isinstance(getattr(o, k), int) else float(v))
     return o
 

@@ -68,6 +68,7 @@ int validate_options(const cpd_options* o) {
   if (o->block_threads < 0 || o->block_threads > 1024 || (o->block_threads % 32) != 0)
     return CPD_ERR_INVALID_ARG;
   if (!(o->mu_min >= 0.0) || o->timeout_cycles < 0) return CPD_ERR_INVALID_ARG;
+  if (o->precond != CPD_PRECOND_JACOBI && o->precond != CPD_PRECOND_BLOCK) return CPD_ERR_INVALID_ARG;
   return CPD_OK;
 }
 
@@ -94,6 +95,7 @@ struct SolvePlan {
   int n_full;
   // device buffers
   DevResult* res = nullptr;
+  int* err = nullptr;           // CPD_ERR_TIMEOUT once a bounded device wait ran out
   double* hist = nullptr;
   int* cgtab = nullptr; int cgtab_len = 0;
   float* W_core = nullptr;     // balanced factors after the core dGN (core space)
@@ -101,6 +103,8 @@ struct SolvePlan {
   float* gscratch = nullptr;
   int big_in_smem = 1;
   size_t dgn_smem = 0;
+  int cluster = 0;              // CTAs of the cluster solver for a large core (0: one CTA)
+  size_t cluster_smem = 0;
   // compression
   int* core_dims_dev = nullptr;
   float* U = nullptr; float* sigma = nullptr; float* G = nullptr; float* Y0 = nullptr; float* Y1 = nullptr;
@@ -117,15 +121,24 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
   for (int l = 0; l < CPD_MAX_ORDER; ++l) cmax[l] = 1;
   for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
   p.res = c.take<DevResult>(1);
+  p.err = c.take<int>(1);
   p.hist = c.take<double>((size_t)o.maxiter + 1);
   p.cgtab_len = o.maxiter + o.refine_maxiter;
   p.cgtab = c.take<int>((size_t)p.cgtab_len + 1);
   Shape sc; make_shape(sc, L, cmax, R);
   p.W_core = c.take<float>(sc.n);
-  size_t smem_big = dgn_smem_bytes_host(L, cmax, R, 1);
+  size_t smem_big = dgn_smem_bytes_host(L, cmax, R, 1, o.precond);
   p.big_in_smem = smem_big <= smem_limit() ? 1 : 0;
-  p.dgn_smem = dgn_smem_bytes_host(L, cmax, R, p.big_in_smem);
+  p.dgn_smem = dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond);
   if (!p.big_in_smem) p.gscratch = c.take<float>(dgn_gscratch_floats_host(L, cmax, R));
+  // a core of 8192 entries or more (or one beyond a CTA's shared memory) is
+  // solved by a cluster, each CTA holding a slice of it (FP32 tensors only)
+  if ((sc.N >= 8192 || !p.big_in_smem) && (o.compress || p.dtype == CPD_F32)) {
+    for (int cs : {16, 8}) {
+      const size_t sm = dgn_cluster_smem_bytes_host(L, cmax, R, cs, o.precond);
+      if (sm <= smem_limit() && sc.N / cmax[0] >= cs) { p.cluster = cs; p.cluster_smem = sm; break; }
+    }
+  }
   p.n_full = 0;
   for (int l = 0; l < L; ++l) p.n_full += R * p.idims[l];
   p.W_full = c.take<float>(p.n_full);
@@ -165,9 +178,9 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
     p.resq = c.take<double>(2);
     p.rG = c.take<float>(p.n_full);
     p.rhist = c.take<double>((size_t)o.refine_maxiter + 1);
-    size_t sm = refine_step_smem_bytes(L, p.dims, R, 1);
+    size_t sm = refine_step_smem_bytes(L, p.dims, R, 1, o.precond);
     p.r_vec_in_smem = sm <= smem_limit() ? 1 : 0;
-    p.r_smem = refine_step_smem_bytes(L, p.dims, R, p.r_vec_in_smem);
+    p.r_smem = refine_step_smem_bytes(L, p.dims, R, p.r_vec_in_smem, o.precond);
     if (!p.r_vec_in_smem) p.rvecs = c.take<float>((size_t)p.n_full * 8 + 1024);
   }
 }
@@ -202,7 +215,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       View3 v{1, p.dims[l], c, l > 0 ? p.core_dims_dev : nullptr, l};
       CK(cudaMemsetAsync(p.G, 0, sizeof(float) * (size_t)p.dims[l] * p.dims[l], st));
       if (l == 0 && o.gram_precision == CPD_GRAM_BF16) {
-        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
+        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st, p.err,
+                                               o.timeout_cycles));
       } else {
         PL("gram_fp32", launch_gram_simt(cur, v, a_max, p.G, st));
       }
@@ -227,7 +241,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       View3 v{a, p.dims[l], c, nullptr, 0};
       CK(cudaMemsetAsync(p.G, 0, sizeof(float) * (size_t)p.dims[l] * p.dims[l], st));
       if (l == 0 && o.gram_precision == CPD_GRAM_BF16)
-        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st));
+        PL("gram_bf16_tc", launch_gram_bf16_tc(T, p.dims[0], c, p.G, p.tc_scratch, p.tc_scratch_bytes, st, p.err,
+                                               o.timeout_cycles));
       else
         PL("gram_fp32", launch_gram_simt(T, v, a, p.G, st));
       EigArgs ea{p.G, p.idims[l], p.P[l], p.U + offU, p.sigma + offS, p.core_dims_dev + l,
@@ -255,6 +270,85 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
   return CPD_OK;
 }
 
+// dGN iterations on the full tensor T from the factors Wr (stacked, in place):
+// each iteration one pass over T and one single-CTA step, at most `maxiter`
+// of them, the state already primed (launch_refine_init); trace records from
+// slot `slot0`.  While st is being captured (and `side` is given) the
+// iterations are the body of a conditional while node.
+int enqueue_refine(SolvePlan& p, const cpd_options& o, const void* T, int L, int R, float* Wr, int maxiter,
+                   int slot0, int cgtab_len, double* trace, int trace_cap, cudaStream_t st, cudaStream_t side,
+                   int* refine_loop) {
+  RefinePassArgs pa{};
+  pa.T = static_cast<const float*>(T); pa.L = L; pa.R = R; pa.W = Wr; pa.G = p.rG; pa.esq = p.resq;
+  for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = p.dims[l];
+  pa.done = p.rdone;
+  pa.err = p.err; pa.budget = o.timeout_cycles;
+  RefineStepArgs sa{};
+  sa.L = L; sa.R = R; sa.W = Wr; sa.G = p.rG; sa.esq = p.resq; sa.state = p.rstate;
+  for (int l = 0; l < CPD_MAX_ORDER; ++l) sa.dims[l] = p.dims[l];
+  sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = maxiter;
+  sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.mu_min = o.mu_min; sa.seed = o.seed; sa.hist = p.rhist;
+  sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = slot0; sa.done = p.rdone;
+  sa.cgtab = p.cgtab; sa.cgtab_len = cgtab_len;
+  sa.err = p.err;
+  sa.precond = o.precond;
+  const int rthreads = 1024;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (side != nullptr && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
+    // iteration 0, then a while node whose body is one iteration; every
+    // exit of the step kernel sets the condition, so the graph runs only
+    // the iterations the stop tests allow (at most refine_maxiter)
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+    sa.use_cond = 1; sa.cond = h;
+    pa.want_tsq = 1; sa.j = 0;
+    PL("refine_pass", launch_refine_pass(pa, st));
+    PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+    CK(cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    pa.want_tsq = 0; sa.j_from_state = 1;
+    cudaError_t e = launch_refine_pass(pa, side);
+    if (e == cudaSuccess) e = launch_refine_step(sa, rthreads, p.r_smem, side);
+    cudaGraph_t body = nullptr;                 // owned by the conditional node
+    const cudaError_t ee = cudaStreamEndCapture(side, &body);
+    CK(e);
+    CK(ee);
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (refine_loop) *refine_loop = 1;
+  } else {
+    // under profiling the host reads the stop flag after each step and
+    // launches no further iterations, as the graph loop does (the stage
+    // times then hold only the iterations that run)
+    const bool watch = profile_enabled() && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+                       cs == cudaStreamCaptureStatusNone;
+    for (int j = 0; j <= maxiter; ++j) {
+      pa.want_tsq = (j == 0);
+      PL("refine_pass", launch_refine_pass(pa, st));
+      sa.j = j;
+      PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
+      if (watch) {
+        int done = 0;
+        CK(cudaMemcpyAsync(&done, p.rdone, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (done) break;
+      }
+    }
+  }
+  return CPD_OK;
+}
+
 // The launch sequence of one solve (Fig. "tensorfox-flow"), enqueued on st.
 // `side` (optional) is an idle stream on which, while st is being captured,
 // the refinement iterations are captured as the body of a conditional while
@@ -264,6 +358,7 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
                   const float* W0, float* W_out, float* lambda_out, double* trace, cudaStream_t st,
                   cudaStream_t side = nullptr, int* refine_loop = nullptr) {
   const int trace_cap = trace ? (o.maxiter + o.refine_maxiter) : 0;
+  CK(cudaMemsetAsync(p.err, 0, sizeof(int), st));
 
   // ---- compression and initial factors -----------------------------------------
   DgnArgs a{};
@@ -287,7 +382,7 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
     a.s_f64 = dtype == CPD_F64;
   }
   a.seed = o.seed; a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b;
-  a.maxiter = o.maxiter; a.mu0 = -1.0; a.mu_min = o.mu_min; a.k0 = 0;
+  a.maxiter = o.maxiter; a.mu0 = -1.0; a.mu_min = o.mu_min; a.precond = o.precond; a.k0 = 0;
   a.big_in_smem = p.big_in_smem; a.gscratch = p.gscratch;
   a.hist = p.hist; a.trace = trace; a.trace_cap = trace_cap; a.trace_slot0 = 0;
   a.W_out = p.W_core; a.res = p.res;
@@ -295,7 +390,21 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
   int cmax[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) cmax[l] = o.compress ? p.P[l] : p.idims[l];
   Shape sc; make_shape(sc, L, cmax, R);
-  PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
+  if (p.cluster > 0) {
+    cudaError_t ce;
+    {
+      ProfScope ps_(st, "dgn_core");
+      ce = launch_dgn_cluster(L, a, threads_for(&o, sc.n), p.cluster, p.cluster_smem, st);
+    }
+    if (ce == cudaErrorInvalidConfiguration) {   // the device cannot place the cluster: one CTA
+      (void)cudaGetLastError();
+      PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
+    } else {
+      CK(ce);
+    }
+  } else {
+    PL("dgn_core", launch_dgn_core(L, a, threads_for(&o, sc.n), p.dgn_smem, st));
+  }
 
   // ---- uncompression, refinement, output ---------------------------------------------
   const float* Wfinal = p.W_core;
@@ -307,71 +416,9 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
     float* Wr = p.W_full;
     if (!o.compress) CK(cudaMemcpyAsync(Wr, p.W_core, sizeof(float) * p.n_full, cudaMemcpyDeviceToDevice, st));
     PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
-    RefinePassArgs pa{};
-    pa.T = static_cast<const float*>(T); pa.L = L; pa.R = R; pa.W = Wr; pa.G = p.rG; pa.esq = p.resq;
-    for (int l = 0; l < CPD_MAX_ORDER; ++l) pa.dims[l] = p.dims[l];
-    pa.done = p.rdone;
-    RefineStepArgs sa{};
-    sa.L = L; sa.R = R; sa.W = Wr; sa.G = p.rG; sa.esq = p.resq; sa.state = p.rstate;
-    for (int l = 0; l < CPD_MAX_ORDER; ++l) sa.dims[l] = p.dims[l];
-    sa.vecs = p.rvecs; sa.vec_in_smem = p.r_vec_in_smem; sa.maxiter = o.refine_maxiter;
-    sa.tol = o.tol; sa.cg_a = o.cg_a; sa.cg_b = o.cg_b; sa.mu_min = o.mu_min; sa.seed = o.seed; sa.hist = p.rhist;
-    sa.trace = trace; sa.trace_cap = trace_cap; sa.trace_slot0 = o.maxiter; sa.done = p.rdone;
-    sa.cgtab = p.cgtab; sa.cgtab_len = p.cgtab_len;
-    const int rthreads = 1024;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (side != nullptr && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
-      // iteration 0, then a while node whose body is one iteration; every
-      // exit of the step kernel sets the condition, so the graph runs only
-      // the iterations the stop tests allow (at most refine_maxiter)
-      cudaGraph_t g = nullptr;
-      const cudaGraphNode_t* deps = nullptr;
-      const cudaGraphEdgeData* ed = nullptr;
-      size_t nd = 0;
-      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
-      cudaGraphConditionalHandle h;
-      CK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
-      sa.use_cond = 1; sa.cond = h;
-      pa.want_tsq = 1; sa.j = 0;
-      PL("refine_pass", launch_refine_pass(pa, st));
-      PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
-      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
-      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-      np.conditional.handle = h;
-      np.conditional.type = cudaGraphCondTypeWhile;
-      np.conditional.size = 1;
-      cudaGraphNode_t node;
-      CK(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
-      CK(cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                       cudaStreamCaptureModeThreadLocal));
-      pa.want_tsq = 0; sa.j_from_state = 1;
-      cudaError_t e = launch_refine_pass(pa, side);
-      if (e == cudaSuccess) e = launch_refine_step(sa, rthreads, p.r_smem, side);
-      cudaGraph_t body = nullptr;                 // owned by the conditional node
-      const cudaError_t ee = cudaStreamEndCapture(side, &body);
-      CK(e);
-      CK(ee);
-      CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-      if (refine_loop) *refine_loop = 1;
-    } else {
-      // under profiling the host reads the stop flag after each step and
-      // launches no further iterations, as the graph loop does (the stage
-      // times then hold only the iterations that run)
-      const bool watch = profile_enabled() && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
-                         cs == cudaStreamCaptureStatusNone;
-      for (int j = 0; j <= o.refine_maxiter; ++j) {
-        pa.want_tsq = (j == 0);
-        PL("refine_pass", launch_refine_pass(pa, st));
-        sa.j = j;
-        PL("refine_step", launch_refine_step(sa, rthreads, p.r_smem, st));
-        if (watch) {
-          int done = 0;
-          CK(cudaMemcpyAsync(&done, p.rdone, sizeof(int), cudaMemcpyDeviceToHost, st));
-          CK(cudaStreamSynchronize(st));
-          if (done) break;
-        }
-      }
-    }
+    const int rc = enqueue_refine(p, o, T, L, R, Wr, o.refine_maxiter, o.maxiter, p.cgtab_len, trace, trace_cap, st,
+                                  side, refine_loop);
+    if (rc != CPD_OK) return rc;
     Wfinal = Wr;
   }
   PL("normalize", launch_normalize(L, p.dims, R, Wfinal, W_out, lambda_out, st));
@@ -432,6 +479,7 @@ void cpd_default_options(cpd_options* o) {
   o->block_threads = 0;
   o->mu_min = 1e-5;
   o->timeout_cycles = 0;
+  o->precond = CPD_PRECOND_JACOBI;
 }
 
 const char* cpd_status_string(int s) {
@@ -480,6 +528,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   if (o.gram_precision == CPD_GRAM_BF16 && !gram_bf16_tc_supported(dims[0], static_cast<const float*>(T)))
     return CPD_ERR_UNSUPPORTED;
   if (o.refine_maxiter > 0 && !pass_ok(L, dims, R)) return CPD_ERR_UNSUPPORTED;
+  if (o.precond == CPD_PRECOND_BLOCK && R > 32) return CPD_ERR_UNSUPPORTED;
   if (!o.compress && !uncompressed_fits(L, dims)) return CPD_ERR_UNSUPPORTED;
 
   SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
@@ -553,7 +602,9 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
 
   if (info) {
     DevResult hr;
+    int werr = 0;
     CK(cudaMemcpyAsync(&hr, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&werr, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     int core_dims[CPD_MAX_ORDER] = {0, 0, 0, 0};
     if (o.compress) CK(cudaMemcpyAsync(core_dims, p.core_dims_dev, sizeof(int) * CPD_MAX_ORDER, cudaMemcpyDeviceToHost, st));
     int r_iters = 0, r_stop = 0, r_cg = 0, r_status = CPD_OK, r_steps = 0; double r_err = 0.0, r_mu = 0.0;
@@ -577,6 +628,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
       info->refine_rel_err = r_err; info->mu = r_mu;
       if (r_status != CPD_OK) info->status = r_status;
     }
+    if (werr != 0) info->status = werr;        // a bounded device wait ran out
   }
   CK(cudaGetLastError());
   return CPD_OK;

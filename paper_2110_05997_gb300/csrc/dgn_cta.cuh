@@ -11,12 +11,11 @@
 
 namespace cpdk {
 
-__host__ __device__ inline size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem) {
+__host__ __device__ inline size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem, int blk = 0) {
   Shape s; make_shape(s, L, d, R);
-  const size_t RR = (size_t)R * R;
   size_t f = 0;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };   // 16-byte granules
-  f += up(L * RR) + up((size_t)L * L * RR) + 2 * up(L * RR) + 3 * up((size_t)L * R);
+  f += small_buf_floats(L, R, blk);
   f += 7 * up((size_t)s.n);
   if (big_in_smem) {
     const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
@@ -35,19 +34,11 @@ __host__ __device__ inline size_t dgn_gscratch_floats(int L, const int* d, int R
 // Carve the solver's buffers: small ones always in shared memory, tensor-sized
 // ones in shared memory when big_in_smem, else in the global scratch.
 __device__ inline void carve(const Shape& s, Bufs& b, unsigned char* smem, float* gscratch,
-                      int big_in_smem, float** Sbuf) {
+                      int big_in_smem, float** Sbuf, int blk = 0) {
   const int L = s.L, R = s.R;
-  const size_t RR = (size_t)R * R;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
   b.red = reinterpret_cast<double*>(smem);
-  float* p = reinterpret_cast<float*>(smem + 128 * sizeof(double));
-  b.gram = p; p += up(L * RR);
-  b.Pi2 = p; p += up((size_t)L * L * RR);
-  b.Xm = p; p += up(L * RR);
-  b.Ym = p; p += up(L * RR);
-  b.msq = p; p += up((size_t)L * R);
-  b.gam = p; p += up((size_t)L * R);
-  b.sc = p; p += up((size_t)L * R);
+  float* p = carve_small(b, reinterpret_cast<float*>(smem + 128 * sizeof(double)), L, R, blk);
   float** vecs[7] = {&b.W, &b.G, &b.X, &b.Rr, &b.P, &b.Z, &b.Tmp};
   for (int v = 0; v < 7; ++v) { *vecs[v] = p; p += up((size_t)s.n); }
   const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
@@ -131,7 +122,7 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
   }
   __syncthreads();
   Bufs b; float* Sbuf;
-  carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf);
+  carve(s, b, smem_raw, a.gscratch, a.big_in_smem, &Sbuf, a.precond);
 
   double normS, meanabs;
   load_tensor(s, a.S, a.s_f64, Sbuf, b.red, normS, meanabs);
@@ -186,9 +177,11 @@ __device__ void dgn_run(const DgnArgs& a, unsigned char* smem_raw) {
     if (threadIdx.x == 0)
       s_maxit = (a.k0 + k <= a.cgtab_len) ? a.cgtab[a.k0 + k] : cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
     grams_pi<L>(s, b);                         // its first barrier publishes s_maxit
-    regularize<L>(s, b, mu);
+    if (a.precond) regularize_block<L>(s, b, mu);
+    else regularize<L>(s, b, mu);
     const int maxit = s_maxit;
-    const int its = (s.n <= (int)blockDim.x) ? pcg_owned<L>(s, b, mu, maxit, a.tol) : pcg<L>(s, b, mu, maxit, a.tol);
+    const int its = a.precond ? pcg_block<L>(s, b, mu, maxit, a.tol)
+                    : (s.n <= (int)blockDim.x) ? pcg_owned<L>(s, b, mu, maxit, a.tol) : pcg<L>(s, b, mu, maxit, a.tol);
     double pred_drop, step;
     finish_step<L>(s, b, pred_drop, step);
     core_pass<L>(s, b, fsq, ginf);

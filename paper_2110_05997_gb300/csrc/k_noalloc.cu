@@ -76,6 +76,8 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   if (o.block_threads < 0 || o.block_threads > 1024 || (o.block_threads % 32) != 0)
     return CPD_ERR_INVALID_ARG;
   if (!(o.mu_min >= 0.0) || o.timeout_cycles < 0) return CPD_ERR_INVALID_ARG;
+  if (o.precond != CPD_PRECOND_JACOBI && o.precond != CPD_PRECOND_BLOCK) return CPD_ERR_INVALID_ARG;
+  if (o.precond == CPD_PRECOND_BLOCK && R > 32) return CPD_ERR_UNSUPPORTED;
   int d[CPD_MAX_ORDER] = {1, 1, 1, 1};
   long long n = 0;
   double N = 1.0;
@@ -93,7 +95,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return CPD_ERR_CUDA;
-  const size_t smem = dgn_smem_bytes_host(L, d, R, 1);
+  const size_t smem = dgn_smem_bytes_host(L, d, R, 1, o.precond);
   if (N > 2.0e9 || smem > (size_t)lim) return CPD_ERR_WORKSPACE;   // T must fit the CTA's shared memory
 
   void* base = nullptr;
@@ -115,7 +117,7 @@ extern "C" int cpd_dgn_solve_noalloc(const void* T, int dtype, int L, const int6
   a.S = T; a.s_f64 = (dtype == CPD_F64);
   a.W0 = W0; a.init = o.init; a.seed = o.seed;
   a.tol = o.tol; a.tau = o.tau; a.cg_a = o.cg_a; a.cg_b = o.cg_b; a.maxiter = o.maxiter;
-  a.mu0 = -1.0; a.mu_min = o.mu_min; a.k0 = 0;
+  a.mu0 = -1.0; a.mu_min = o.mu_min; a.precond = o.precond; a.k0 = 0;
   a.big_in_smem = 1; a.gscratch = nullptr;
   a.hist = hist; a.trace = nullptr; a.trace_cap = 0; a.trace_slot0 = 0;
   a.W_out = Wc; a.res = res;

@@ -36,7 +36,39 @@ struct Bufs {
   float* gram; float* Pi2; float* Xm; float* Ym;              // L*R*R, L*L*R*R, L*R*R, L*R*R
   float* msq; float* gam; float* sc;                          // L*R each
   double* red;                                                // >= 128 doubles, shared
+  float* Minv = nullptr;      // block preconditioner: (Pi^(l) + mu diag gamma^(l))^{-1}, L*R*R
+  double* Bd = nullptr;       // its FP64 Cholesky workspace, L*R*R
 };
+
+// Floats of the solver's small buffers (R x R Grams and Pi matrices, the
+// Hv intermediates, L x R vectors), plus with the block preconditioner its
+// inverse blocks and their FP64 workspace (two floats per double).
+__host__ __device__ inline size_t small_buf_floats(int L, int R, int blk) {
+  const size_t RR = (size_t)R * R;
+  auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
+  size_t f = up(L * RR) + up((size_t)L * L * RR) + 2 * up(L * RR) + 3 * up((size_t)L * R);
+  if (blk) f += up(L * RR) + 2 * up(L * RR);
+  return f;
+}
+
+// Carve the small buffers from p (16-byte aligned); returns the end.
+__device__ inline float* carve_small(Bufs& b, float* p, int L, int R, int blk) {
+  const size_t RR = (size_t)R * R;
+  auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
+  b.gram = p; p += up(L * RR);
+  b.Pi2 = p; p += up((size_t)L * L * RR);
+  b.Xm = p; p += up(L * RR);
+  b.Ym = p; p += up(L * RR);
+  b.msq = p; p += up((size_t)L * R);
+  b.gam = p; p += up((size_t)L * R);
+  b.sc = p; p += up((size_t)L * R);
+  b.Minv = nullptr; b.Bd = nullptr;
+  if (blk) {
+    b.Minv = p; p += up(L * RR);
+    b.Bd = reinterpret_cast<double*>(p); p += 2 * up(L * RR);
+  }
+  return p;
+}
 
 // Iteration state, kept in shared memory by the single-CTA solvers and in
 // global memory between the kernels of the refinement loop.
@@ -115,6 +147,79 @@ __device__ void regularize(const Shape& s, const Bufs& b, double mu) {
     b.gam[q] = g;
     const float m = fmaf(muf, g, a);
     b.msq[q] = m > 0.f ? rsqrtf(m) : 1.f;
+  }
+  __syncthreads();
+}
+
+// Block-Jacobi preconditioner (the diagonal blocks of J^T J + mu D; by the
+// theorem on J^T J of Sec. 3.5.3 block l is Pi^(l) (x) I_{I_l}, D's block
+// diag(gamma^(l)) (x) I): gamma as in regularize(), then per mode the R x R
+// matrix B_l = Pi^(l) + mu diag(gamma^(l)) in FP64, its Cholesky factor C
+// (one warp per mode, right-looking), C^{-1} by forward substitution (lane j
+// column j) and Minv_l = C^{-T} C^{-1} rounded to FP32.  msq is set to 1:
+// the block PCG works in the original variables.  R <= 32; needs L warps.
+template <int L>
+__device__ void regularize_block(const Shape& s, const Bufs& b, double mu) {
+  const int R = s.R, RR = R * R;
+  float mx = 0.f;
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+    const int l = q / R, r = q - l * R;
+    float p = 1.f;
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (j != l) p *= sqrtf(fmaxf(b.gram[j * RR + r * R + r], 0.f));
+    b.gam[q] = p;
+    mx = fmaxf(mx, p);
+  }
+  const float gmax = block_max(mx, b.red);
+  for (int q = threadIdx.x; q < L * R; q += blockDim.x) { b.gam[q] *= gmax; b.msq[q] = 1.f; }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * RR; q += blockDim.x) {
+    const int l = q / RR, rc = q - l * RR, r = rc / R, c = rc - r * R;
+    double v = (double)b.Pi2[(l * L + l) * RR + rc];
+    if (r == c) v += mu * (double)b.gam[l * R + r];
+    b.Bd[q] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < L) {
+    double* B = b.Bd + warp * RR;
+    for (int k = 0; k < R; ++k) {                  // lower Cholesky factor in place
+      if (lane == 0) B[k * R + k] = sqrt(fmax(B[k * R + k], 1e-300));
+      __syncwarp();
+      const double dk = B[k * R + k];
+      for (int i = k + 1 + lane; i < R; i += 32) B[i * R + k] /= dk;
+      __syncwarp();
+      for (int e = lane; e < (R - k - 1) * (R - k - 1); e += 32) {
+        const int i = k + 1 + e / (R - k - 1), j = k + 1 + e % (R - k - 1);
+        if (j <= i) B[i * R + j] -= B[i * R + k] * B[j * R + k];
+      }
+      __syncwarp();
+    }
+    // C^{-1}: column j = lane by forward substitution, kept in the lane until
+    // every lane has read C, then written over C's lower triangle
+    float* Mi = b.Minv + warp * RR;
+    double ci[32];
+    const int j = lane;
+    if (j < R) {
+      for (int i = 0; i < R; ++i) {
+        if (i < j) { ci[i] = 0.0; continue; }
+        double v = (i == j) ? 1.0 : 0.0;
+        for (int t = j; t < i; ++t) v -= B[i * R + t] * ci[t];
+        ci[i] = v / B[i * R + i];
+      }
+    }
+    __syncwarp();
+    if (j < R)
+      for (int i = j; i < R; ++i) B[i * R + j] = ci[i];
+    __syncwarp();
+    // Minv = C^{-T} C^{-1}: Minv[r][c] = sum_{t >= max(r, c)} Ci[t][r] Ci[t][c]
+    for (int e = lane; e < RR; e += 32) {
+      const int r = e / R, c = e - r * R;
+      double v = 0.0;
+      for (int t = (r > c ? r : c); t < R; ++t) v += B[t * R + r] * B[t * R + c];
+      Mi[e] = (float)v;
+    }
   }
   __syncthreads();
 }
@@ -221,6 +326,73 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
     }
     __syncthreads();
     if ((double)rr < tol) break;
+  }
+  return its;
+}
+
+// Preconditioned CG (App. A, the standard form) on (J^T J + mu D) x = A^T b
+// with the block-Jacobi preconditioner of regularize_block(): z = M^{-1} r is,
+// per mode, Z^(l) = R^(l) Minv_l.  Vectors: x in b.X, r in b.Rr, z in b.Tmp,
+// p in b.P, q = (J^T J + mu D) p in b.Z.  Stop on r^T z < tol (the split
+// form's ||M^{-1/2} r||^2) or maxit; x is left in b.X in the original
+// variables (msq = 1).  Returns the iterations run.
+template <int L>
+__device__ int pcg_block(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const int n = s.n, R = s.R, RR = R * R;
+  auto minv = [&](int j, const float* v) {          // (V^(l) Minv_l)[i, r] for entry j = (l, i, r)
+    int l, i, r; decode_j<L>(s, j, l, i, r);
+    const float* vr = v + s.off[l] + i;
+    const float* M = b.Minv + l * RR + r;
+    const int d = s.d[l];
+    float z = 0.f;
+    for (int t = 0; t < R; ++t) z = fmaf(vr[t * d], M[t * R], z);
+    return z;
+  };
+  for (int j = threadIdx.x; j < n; j += blockDim.x) { b.Rr[j] = b.G[j]; b.X[j] = 0.f; }
+  __syncthreads();
+  float v[1] = {0.f};
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float z = minv(j, b.Rr);
+    b.Tmp[j] = z; b.P[j] = z;
+    v[0] = fmaf(b.Rr[j], z, v[0]);
+  }
+  float rz0[1];
+  block_sum_f<1>(v, rz0, b.red);
+  float rz = rz0[0];
+  int its = 0;
+  const float muf = (float)mu;
+  for (int it = 0; it < maxit; ++it) {
+    hv_xy<L>(s, b, b.P);
+    float pqf[1] = {0.f};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      int l, i, r; decode_j<L>(s, j, l, i, r);
+      const float q = hv_entry<L>(s, b, b.P, l, i, r) + muf * b.gam[l * R + r] * b.P[j];
+      b.Z[j] = q;
+      pqf[0] = fmaf(b.P[j], q, pqf[0]);
+    }
+    float pq[1];
+    block_sum_f<1>(pqf, pq, b.red);
+    if (!(pq[0] > 0.f)) break;
+    const float af = rz / pq[0];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      b.X[j] = fmaf(af, b.P[j], b.X[j]);
+      b.Rr[j] = fmaf(-af, b.Z[j], b.Rr[j]);
+    }
+    __syncthreads();
+    float rzf[1] = {0.f};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const float z = minv(j, b.Rr);
+      b.Tmp[j] = z;
+      rzf[0] = fmaf(b.Rr[j], z, rzf[0]);
+    }
+    float rzn[1];
+    block_sum_f<1>(rzf, rzn, b.red);
+    const float bf = rz > 0.f ? rzn[0] / rz : 0.f;
+    rz = rzn[0];
+    its = it + 1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) b.P[j] = fmaf(bf, b.P[j], b.Tmp[j]);
+    __syncthreads();
+    if ((double)rz < tol) break;
   }
   return its;
 }
@@ -556,9 +728,13 @@ __device__ inline int stop_test(int k, int maxiter, double tol, double e, double
   return CPD_STOP_NONE;
 }
 
-// Divergence threshold of stop test 7: max(1, ||S||^2) / (1e-16 + tol).
+// Divergence threshold of stop test 7: max(1, ||S||^2) / (1e-16 + tol), capped
+// at a relative error of 1e4 for the FP32 iteration: a trajectory that far
+// off has diverged, and the printed bound (>= 1e6 with tol = 1e-6) lies where
+// FP32 residuals overflow; the cap keeps the last iterate finite.
+constexpr double kFp32DivergenceCap = 1e4;
 __device__ inline double divergence_threshold(double normS, double tol) {
-  return fmax(1.0, normS * normS) / (1e-16 + tol);
+  return fmin(fmax(1.0, normS * normS) / (1e-16 + tol), kFp32DivergenceCap);
 }
 
 // cg_maxiter(k) for k = 1..len into tab[k] by all threads of the CTA (the FP64

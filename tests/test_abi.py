@@ -45,7 +45,7 @@ def test_defaults_are_the_thesis_defaults(cpd):
     assert o.cg_a == 0.4 and o.cg_b == 0.9
     assert o.st_mlsvd == 1 and o.compress == 1 and o.init == 0
     # the FP32 damping floor (not in the thesis) and the default wait budget
-    assert o.mu_min == 1e-5 and o.timeout_cycles == 0
+    assert o.mu_min == 1e-5 and o.timeout_cycles == 0 and o.precond == 0
     assert cpd.cpd_status_string(-1) == "invalid argument"
 
 
@@ -109,6 +109,10 @@ def test_validation_before_launch(cpd):
     assert solve(3, (4, 4, 4), 2, opts=bad) == -1
     bad = cpd.cpd_default_options(timeout_cycles=-5)
     assert solve(3, (4, 4, 4), 2, opts=bad) == -1
+    bad = cpd.cpd_default_options(precond=2)
+    assert solve(3, (4, 4, 4), 2, opts=bad) == -1
+    blk = cpd.cpd_default_options(precond="block")     # R x R FP64 blocks: ranks up to 32
+    assert solve(3, (40, 40, 40), 33, opts=blk) == -6
     # dGN on T itself (one CTA, 32-bit entry indices) is refused beyond 2^31 - 1024
     # entries, before anything is sized or launched
     o_unc = cpd.cpd_default_options(compress=0)

@@ -99,12 +99,23 @@ def test_compress_exact_low_multilinear_rank(cpd):
     assert np.linalg.norm(rec - T) <= 1e-5 * np.linalg.norm(T)
 
 
-# every padded rank (8, 12, 16, 32, 64), one to four rows per thread (I1 up
-# to 1024), orders 3 and 4, ragged last batches of fibres
+def _tensor_core_pass(dims, R):
+    """The shapes the refinement pass runs on the tensor cores (csrc/k_refine_tc.cu);
+    the others run the CUDA-core pass."""
+    nf = int(np.prod(dims[1:]))
+    return R <= 16 and dims[0] % 4 == 0 and 4 <= dims[0] <= 256 and nf < 2 ** 31 - 128
+
+
+# every padded rank of the CUDA-core pass (8, 12, 16, 32, 64), one to four rows
+# per thread (I1 up to 1024), orders 3 and 4, ragged last batches of fibres; on
+# the tensor-core pass one and two row chunks (I1 = 200, 128, 256), a rank of
+# one, fewer fibres than one tile and ragged last tiles
 @pytest.mark.parametrize("dims,R", [((50, 40, 30), 4), ((20, 18, 16, 14), 3), ((257, 3, 5), 2), ((7, 33, 65), 6),
                                     ((300, 20, 10), 10), ((200, 17, 9), 12), ((40, 30, 20), 16),
                                     ((64, 9, 7), 20), ((33, 10, 6), 40), ((600, 5, 4), 3),
-                                    ((1024, 3, 3), 16), ((20, 18, 16, 14), 12), ((130, 7, 5, 3), 30)])
+                                    ((1024, 3, 3), 16), ((20, 18, 16, 14), 12), ((130, 7, 5, 3), 30),
+                                    ((100, 9, 7, 5), 15), ((128, 20, 10), 8), ((256, 12, 11), 16),
+                                    ((4, 50, 3), 1), ((40, 3, 2), 5), ((100, 60, 50), 15)])
 def test_refine_eval_matches_oracle(cpd, dims, R):
     g = np.random.default_rng(sum(dims) + R)
     T = g.standard_normal(dims).astype(np.float32).astype(np.float64)
@@ -114,9 +125,25 @@ def test_refine_eval_matches_oracle(cpd, dims, R):
     f = O.residual(T, Ws)
     ref = stacked(O.neg_gradient(f, Ws))
     e = esq.cpu().numpy()
+    # the residual is FP32-accurate on both passes
     assert abs(e[0] - np.sum(f * f)) <= 1e-5 * np.sum(f * f)
     assert abs(e[1] - np.sum(T * T)) <= 1e-5 * np.sum(T * T)
-    assert np.linalg.norm(gr.cpu().numpy() - ref) <= 2e-5 * np.linalg.norm(ref)
+    got = gr.cpu().numpy()
+    if not _tensor_core_pass(dims, R):
+        assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
+        return
+    # tensor-core pass: the MTTKRP of e takes BF16 products (each operand
+    # rounded to 8 significant bits: relative error <= 2^-8 per product) with
+    # FP32 accumulation, so entry (l, i, r) is within 2^-7 of the same MTTKRP
+    # taken over absolute values, sum |e| |prod of the other factors| (factor 2
+    # for the accumulation), plus the FP32 residual's own rounding
+    bound = stacked(O.neg_gradient(np.abs(f), [np.abs(w) for w in Ws]))
+    bound_t = stacked(O.neg_gradient(np.abs(T), [np.abs(w) for w in Ws]))
+    tol = 2.0 ** -7 * bound + 1e-6 * bound_t
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (float(np.max(err / tol)), dims, R)
+    # and the bound is not vacuous: the error is far below the gradient's size
+    assert np.linalg.norm(got - ref) <= 1e-2 * np.linalg.norm(ref)
 
 
 def _solve(cpd, T, R, **kw):
