@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Throughput of the MLSVD-compressed damped Gauss-Newton CPD on one GB300.
 
-Workload (one step = one whole CPD through the C ABI): a 200x200x200 FP32
-tensor of rank 10 with pairwise factor collinearity 0.5 and relative noise
-1e-4 (synthetic, seeded), compressed by ST-MLSVD to a <= 10x10x10 core (the
-first-mode Gram on BF16 tensor cores by default, --gram fp32 for CUDA cores),
-dGN on the core from the MLSVD-energy start, uncompression and FP32
-refinement iterations on T, output normalisation.  Metric: CPDs per second, with the
-fit of every result checked against the FP64 oracle's (within 1e-6).
+Default workload (one step = one whole CPD through the C ABI): the largest
+single-GPU configuration, a 100x100x100x100 FP32 tensor (400 MB) of rank 15
+with Gaussian factors and relative noise 1e-5 (synthetic, seeded),
+compressed by ST-MLSVD to a <= 15^4 core (the first-mode Gram on BF16 tensor
+cores, --gram fp32 for CUDA cores), dGN on the core from the random start
+(seed 0; the MLSVD-energy start stalls on this problem in the method itself),
+uncompression, FP32 refinement iterations on T, output normalisation.
+--workload compressed200 runs the 200^3 rank-10 configuration (collinearity
+0.5, noise 1e-4, MLSVD-energy start) instead.  Metric: CPDs per second, with
+the fit of every result checked against the FP64 oracle's (within 1e-6).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +47,7 @@ def peaks():
             d = json.load(fh)
         return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
                     bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
-                    sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured")
+                    sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured (MEASURED_PEAKS.json)")
     return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
 
 
@@ -104,17 +107,35 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(mhz))
 
 
-def workload():
-    c = synth.c2_compressed()
-    return c["T"], c["R"]
+# single-tensor workloads: generator, solver options, name
+WORKLOADS = {
+    "order4": dict(gen=synth.c3_order4, opts=dict(init="random", seed=0),
+                   name="mlsvd_dgn_100x100x100x100_r15_noise1e-5_random_start"),
+    "compressed200": dict(gen=synth.c2_compressed, opts=dict(),
+                          name="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4"),
+}
+
+
+def workload(name):
+    w = WORKLOADS[name]
+    c = w["gen"]()
+    return c["T"], c["R"], w["opts"], w["name"]
+
+
+def oracle_options(extra):
+    import oracle as O
+    o = dict(refine_maxiter=REFINE_MAXITER)
+    o.update(extra)
+    return O.Options(**o)
 
 
 # sources whose kernels a stage times; a DRAM-traffic figure recorded in
 # profiles/traffic.json is reported only while these files are unchanged
 STAGE_SOURCES = {
-    "dgn_core": ["k_dgn.cu", "dgn_cta.cuh", "solver.cuh", "common.cuh", "kernels.h"],
-    "gram_bf16_tc": ["k_gram_tc.cu", "kernels.h"],
-    "refine_pass": ["k_refine_pass3.cu", "refine_pass.cuh", "solver.cuh", "common.cuh", "kernels.h"],
+    "dgn_core": ["k_dgn.cu", "k_dgn_cluster.cu", "dgn_cta.cuh", "solver.cuh", "common.cuh", "kernels.h"],
+    "gram_bf16_tc": ["k_gram_tc.cu", "tc_common.cuh", "kernels.h"],
+    "refine_pass": ["k_refine_tc.cu", "tc_common.cuh", "k_refine_pass3.cu", "k_refine_pass4.cu", "refine_pass.cuh",
+                    "solver.cuh", "common.cuh", "kernels.h"],
 }
 
 
@@ -145,12 +166,12 @@ def measured_traffic(stage: str):
 
 
 def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: dict, clk_mhz,
-                gram_bf16: bool = True):
+                gram_bf16: bool = True, sms: int = 152):
     """Roofline entry of a stage: algorithmic bytes or flops per launch over
-    its measured average launch time."""
+    its measured average launch time.  The FP32 peak is derived (SM count of
+    the device x 128 FMA lanes x 2 flops x the sampled SM clock), not measured."""
     N = int(np.prod(dims))
     I1 = int(dims[0])
-    sms = 152
     mhz = clk_mhz or pk["sm_max_mhz"]
     fp32_peak_tf = sms * 128 * 2 * mhz * 1e6 / 1e12          # FP32 FMA pipes, all SMs
     if stage == "refine_pass":
@@ -170,7 +191,8 @@ def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: 
             fls.append(2.0 * int(dims[l]) * Nl)
         fl = sum(fls) / len(fls)
         ach = fl / (per_launch_ms * 1e-3) / 1e12
-        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, unit="TFLOP/s", frac=ach / fp32_peak_tf,
+        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, peak_kind="derived FP32 FMA peak", unit="TFLOP/s",
+                    frac=ach / fp32_peak_tf,
                     algorithmic_per_launch=fl)
     if stage in ("gram_fp32", "gram_bf16_tc"):
         # mode-1 Gram G = T_(1) T_(1)^T: I1^2 * (N / I1) multiply-adds (2 flops each)
@@ -181,7 +203,8 @@ def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: 
             return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
                         algorithmic_per_launch=nbytes, flops=fl)
         ach = fl / (per_launch_ms * 1e-3) / 1e12
-        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, unit="TFLOP/s", frac=ach / fp32_peak_tf,
+        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, peak_kind="derived FP32 FMA peak", unit="TFLOP/s",
+                    frac=ach / fp32_peak_tf,
                     algorithmic_per_launch=fl)
     if stage == "dgn_core":
         # per-iteration flop model of Sec. 4.1.3 ("Overall cost of dGN"), with
@@ -195,18 +218,19 @@ def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: 
         fl = it * ((L * R + L - 1) * Nc + L * R * Nc + R * R * (L + sR) + 3 * R * sR) * 2 \
             + cg * (9 * R + L * R * R) * sR * 2
         ach = fl / (per_launch_ms * 1e-3) / 1e12
-        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, unit="TFLOP/s", frac=ach / fp32_peak_tf,
+        return dict(bound="alu", achieved=ach, peak=fp32_peak_tf, peak_kind="derived FP32 FMA peak", unit="TFLOP/s",
+                    frac=ach / fp32_peak_tf,
                     algorithmic_per_launch=fl)
     ach = 0.0
     return dict(bound="latency", achieved=ach, peak=None, unit="-", frac=None)
 
 
-def cpu_baseline(T, R, ours_W=None, ours_lam=None, budget_s: float = 20.0):
-    """The FP64 oracle, as it stands, on the same tensor: whole CPDs until the
-    budget is spent (at least one)."""
+def cpu_baseline(T, R, extra, name, ours_W=None, ours_lam=None, budget_s: float = 20.0):
+    """The FP64 oracle, as it stands, on the same tensor with the same start:
+    whole CPDs until the budget is spent (at least one)."""
     import oracle as O
     T64 = T.astype(np.float64)
-    opts = O.Options(refine_maxiter=REFINE_MAXITER)
+    opts = oracle_options(extra)
     times, res = [], None
     t_all = time.perf_counter()
     while True:
@@ -217,7 +241,7 @@ def cpu_baseline(T, R, ours_W=None, ours_lam=None, budget_s: float = 20.0):
             break
     Wo, lo, io = res
     out = dict(value=len(times) / sum(times), unit=UNIT, cores=os.cpu_count(), kind="oracle",
-               sample=f"{len(times)} whole CPDs of the 200^3 workload (numpy FP64, default BLAS threads)")
+               sample=f"{len(times)} whole CPDs of {name} (numpy FP64, default BLAS threads)")
     if ours_W is not None:
         fo = O.fit(T64, Wo, lo)
         fg = O.fit(T64, ours_W, ours_lam)
@@ -230,10 +254,11 @@ def cpu_baseline(T, R, ours_W=None, ours_lam=None, budget_s: float = 20.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    T, R = workload()
+    wl = args.workload if args.workload in WORKLOADS else "order4"
+    T, R, extra, name = workload(wl)
     import oracle as O
     T64 = T.astype(np.float64)
-    opts = O.Options(refine_maxiter=REFINE_MAXITER)
+    opts = oracle_options(extra)
     for _ in range(args.warmup):
         O.cpd(T64, R, opts)
     t0 = time.perf_counter()
@@ -244,10 +269,10 @@ def run_reference(args, rank, world):
     line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4", global_batch=1,
+                config=dict(workload=name, tensor_dims=list(T.shape), rank=R, global_batch=1,
                             parallelism="host"),
                 cpu_baseline=dict(kind="oracle", cores=os.cpu_count(), value=v, unit=UNIT,
-                                  sample=f"{args.steps} whole CPDs after {args.warmup} warm-up"),
+                                  sample=f"{args.steps} whole CPDs of {name} after {args.warmup} warm-up"),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -306,11 +331,12 @@ def run_ours(args, rank, world, local_rank):
         return run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush)
     if args.workload == "initnet":
         return run_initnet_workload(args, rank, world, local_rank, torch, cpd, dev, stream, flush)
-    T, R = workload()
+    T, R, extra, wname = workload(args.workload)
     dims = T.shape
     T_flat = synth.flat(T)
     Td = torch.from_numpy(T_flat).to(dev)
-    opts = cpd.cpd_default_options(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    opts = cpd.cpd_default_options(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram, **extra)
     ws = torch.empty(cpd.cpd_workspace_size(dims, R, opts), dtype=torch.uint8, device=dev)
 
     # timed calls read no info record (no host synchronisation inside a step);
@@ -373,7 +399,7 @@ def run_ours(args, rank, world, local_rank):
     roof = None
     if dom[0] is not None:
         per = dom[1]["ms"] / dom[1]["launches"]
-        roof = algorithmic(dom[0], dims, R, infos[-1], per, pk, csum["sm_mhz"])
+        roof = algorithmic(dom[0], dims, R, infos[-1], per, pk, csum["sm_mhz"], sms=sms)
         roof.update(kernel=dom[0], launches=dom[1]["launches"], ms_per_launch=per, traffic=measured_traffic(dom[0]),
                     peak_source=pk["src"], region="separate profiled K-step region, direct launches")
     # the same roofline entry for the other stages that have a bound
@@ -386,7 +412,7 @@ def run_ours(args, rank, world, local_rank):
             # passes after the stop test exit at once: time the working ones
             n = min(n, args.steps * (int(infos[-1].get("refine_iters", 0)) + 1))
         r = algorithmic(k, dims, R, infos[-1], v["ms"] / max(n, 1), pk, csum["sm_mhz"],
-                        gram_bf16=(args.gram == "bf16"))
+                        gram_bf16=(args.gram == "bf16"), sms=sms)
         r.update(traffic=measured_traffic(k), working_launches=n)
         stage_roofs[k] = r
     stages = {k: dict(ms_per_step=v["ms"] / args.steps, launches_per_step=v["launches"] / args.steps)
@@ -394,20 +420,20 @@ def run_ours(args, rank, world, local_rank):
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4", tensor_dims=list(dims),
+                config=dict(workload=wname, tensor_dims=list(dims), start=extra.get("init", "mlsvd"),
                             rank=R, gram_precision=args.gram, refine_maxiter=REFINE_MAXITER,
                             global_batch=world, parallelism=f"independent CPD per GPU x{world}",
                             l2="flushed between steps (256 MB write)", launch="cached CUDA graph per solve"),
                 e2e=e2e, gpu_launches=int(launches), roofline=roof, stage_rooflines=stage_roofs, stages=stages,
                 profiled_ms_per_step=ms_prof / args.steps,
                 clocks=csum, solve=dict(core_iters=info["iters"], core_stop=info["stop_name"],
-                                        core_cg=info["cg_total"], core_dims=info["core_dims"][:3],
+                                        core_cg=info["cg_total"], core_dims=info["core_dims"][:len(dims)],
                                         refine_iters=info["refine_iters"],
                                         refine_rel_err=info["refine_rel_err"]))
     if not args.no_cpu_baseline:
         Wg = [w.double().cpu().numpy() for w in W]
         lg = lam.double().cpu().numpy()
-        cb = cpu_baseline(T, R, Wg, lg, budget_s=args.cpu_budget)
+        cb = cpu_baseline(T, R, extra, wname, Wg, lg, budget_s=args.cpu_budget)
         line["parity"] = cb.pop("parity", None)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
@@ -426,7 +452,10 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
     Tp = torch.from_numpy(flat).to(dev)
     dims = [list(it["T"].shape) for it in items]
     ranks = [it["R"] for it in items]
-    opts = cpd.cpd_default_options()
+    # stop tolerance one decade below the noise level: the fit then agrees with
+    # the oracle's within 1e-6 (with tol = noise the improvement test stops at
+    # rounding-dependent points above the noise floor)
+    opts = cpd.cpd_default_options(tol=1e-7)
     ws = torch.empty(cpd.cpd_batch_workspace_size(dims, ranks, opts), dtype=torch.uint8, device=dev)
 
     def step():
@@ -447,7 +476,7 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
     # what the autotuner chose between: each CTA size forced, one timed step
     cta_ms = {}
     for th in (64, 128, 256):
-        o_th = cpd.cpd_default_options(block_threads=th)
+        o_th = cpd.cpd_default_options(block_threads=th, tol=1e-7)
         with torch.cuda.stream(stream):
             cpd.cpd_batch_solve(Tp, offs, dims, ranks, o_th, stream=stream, workspace=ws, want_infos=False)
             torch.cuda.synchronize()
@@ -460,7 +489,7 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
     pick = np.random.default_rng(7).choice(B, size=min(256, B), replace=False)
     per = [(torch.from_numpy(synth.flat(items[int(b)]["T"]).astype(np.float32)).to(dev), dims[int(b)],
             ranks[int(b)]) for b in pick]
-    popts = cpd.cpd_default_options()
+    popts = cpd.cpd_default_options(tol=1e-7)
     pws = torch.empty(max(cpd.cpd_workspace_size(d, r, popts) for _, d, r in per), dtype=torch.uint8, device=dev)
 
     def per_tensor():
@@ -476,7 +505,7 @@ def run_batch_workload(args, rank, world, local_rank, torch, cpd, dev, stream, f
     line = dict(metric="CPDs/sec (batched uneven CPDs)", value=whole_job_value(B, args.steps, world, ms),
                 unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload="batch_4096_uneven_3rd_order_r2-8_noise1e-6", global_batch=B * world,
+                config=dict(workload="batch_4096_uneven_3rd_order_r2-8_noise1e-6", tol=1e-7, global_batch=B * world,
                             parallelism=f"one persistent launch per GPU x{world}",
                             l2="flushed between steps (256 MB write)"),
                 gpu_launches=int(launches), clocks=clk.summary(),
@@ -570,7 +599,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gram", choices=["fp32", "bf16"], default="bf16")
-    ap.add_argument("--workload", choices=["compressed", "batch", "initnet"], default="compressed")
+    ap.add_argument("--workload", choices=["order4", "compressed200", "batch", "initnet"], default="order4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -55,3 +55,19 @@ def test_traffic_record_is_reported_only_for_unchanged_sources(tmp_path, monkeyp
     monkeypatch.setattr(bench, "sources_sha256", lambda stage: "1" * 64)
     for stage in stale:
         assert bench.measured_traffic(stage) is None
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    import bench
+    ap_default = [ln for ln in open(os.path.join(ROOT, "bench.py")) if '"--workload"' in ln][0]
+    assert 'default="order4"' in ap_default
+    w = bench.WORKLOADS["order4"]
+    assert "100x100x100x100_r15" in w["name"] and w["opts"]["init"] == "random"
+
+
+def test_fp32_peak_is_derived_from_the_sm_count():
+    import bench
+    a = bench.algorithmic("dgn_core", (200, 200, 200), 10, INFO, 0.7, PK, 2000, sms=152)
+    b = bench.algorithmic("dgn_core", (200, 200, 200), 10, INFO, 0.7, PK, 2000, sms=76)
+    assert abs(a["peak"] - 152 * 128 * 2 * 2000e6 / 1e12) < 1e-9
+    assert abs(b["peak"] - a["peak"] / 2) < 1e-9 and "derived" in a["peak_kind"]
