@@ -225,7 +225,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
                  o.gram_precision == CPD_GRAM_BF16 ? 1 : 0};
       PL("eig", launch_eig(ea, st));
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
-      PL("project", launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+      PL(l == 0 ? "project_T" : "project",
+         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];
@@ -261,7 +262,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       for (int j = l + 1; j < L; ++j) c *= p.dims[j];
       View3 v{1, p.dims[l], c, l > 0 ? p.core_dims_dev : nullptr, l};
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
-      PL("project", launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+      PL(l == 0 ? "project_T" : "project",
+         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];

@@ -57,18 +57,32 @@ __device__ __forceinline__ bool jacobi_rot(const Real* H, int m, int p, int q, f
   return true;
 }
 
-// One cyclic sweep of Jacobi with the round-robin parallel ordering (Golub &
-// Van Loan, "parallel Jacobi") on the m x m symmetric H (row-major); V
-// accumulates the rotations.  Per round: one thread per pair forms its
-// rotation; then the round's m/2 disjoint rotations J are applied as
-// H <- J^T H J into the other buffer, one 2x2 block (pair k1 rows, pair k2
-// columns) per work item, and V <- V J in place, one (row, pair) per item.
-// H and Hn swap roles after each round.
+// Pair k of round t of the round-robin parallel ordering on me = m + (m & 1)
+// indices (Golub & Van Loan, "parallel Jacobi"): index 0 stays, the others
+// rotate; p < q, q == m is the padding index of odd m.
+__device__ __forceinline__ void jacobi_pair(int t, int k, int nr, int& p, int& q) {
+  p = 0; q = t + 1;
+  if (k != 0) {
+    int x = t + k, y = t - k + nr;
+    if (x >= nr) x -= nr;
+    if (y >= nr) y -= nr;
+    p = x + 1; q = y + 1;
+  }
+  if (p > q) { const int x = p; p = q; q = x; }
+}
+
+// One cyclic sweep of Jacobi with the round-robin parallel ordering on the
+// m x m symmetric H (row-major); V accumulates the rotations.  Per round: one
+// thread per pair forms its rotation (the identity (1, 0) when skipped);
+// then the round's m/2 disjoint rotations J are applied as H <- J^T H J into
+// the other buffer, one 2x2 block (pair k1 rows, pair k2 columns) per work
+// item, and V <- V J in place, one (row, pair) per item.  The work items
+// recompute the pairs' indices instead of reading them, so that their loads
+// of H and of the rotations issue together.  H and Hn swap roles after each
+// round.
 template <typename Real>
 static __device__ void jacobi_sweep(Real*& H, Real*& Hn, Real* V, int m, float skip) {
   __shared__ Real r_c[kMaxM / 2], r_s[kMaxM / 2];
-  __shared__ int r_p[kMaxM / 2], r_q[kMaxM / 2];
-  __shared__ bool r_act[kMaxM / 2];
   const int me = m + (m & 1), np = me / 2, nr = me - 1;
   const int nblk = np * np;
   // integer quotients of the work-item index by np and m through FP32
@@ -78,48 +92,37 @@ static __device__ void jacobi_sweep(Real*& H, Real*& Hn, Real* V, int m, float s
   for (int t = 0; t < nr; ++t) {
     if (threadIdx.x < np) {
       const int k = threadIdx.x;
-      int p = 0, q = t + 1;
-      if (k != 0) {
-        int x = t + k, y = t - k + nr;
-        if (x >= nr) x -= nr;
-        if (y >= nr) y -= nr;
-        p = x + 1; q = y + 1;
-      }
-      if (p > q) { const int x = p; p = q; q = x; }
+      int p, q;
+      jacobi_pair(t, k, nr, p, q);
       Real c, s;
-      r_act[k] = jacobi_rot(H, m, p, q, skip, c, s);
-      r_p[k] = p; r_q[k] = q; r_c[k] = c; r_s[k] = s;
+      jacobi_rot(H, m, p, q, skip, c, s);
+      r_c[k] = c; r_s[k] = s;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nblk + np * m; e += blockDim.x) {
       if (e < nblk) {
         const int k1 = __float2int_rd(((float)e + 0.5f) * inv_np), k2 = e - k1 * np;
-        const int p1 = r_p[k1], q1 = r_q[k1], p2 = r_p[k2], q2 = r_q[k2];
+        int p1, q1, p2, q2;
+        jacobi_pair(t, k1, nr, p1, q1);
+        jacobi_pair(t, k2, nr, p2, q2);
         const bool r1 = q1 < m, r2 = q2 < m;
+        const Real c1 = r_c[k1], s1 = r_s[k1], c2 = r_c[k2], s2 = r_s[k2];
         const Real a = H[p1 * m + p2];
         const Real b = r2 ? H[p1 * m + q2] : (Real)0;
         const Real cc = r1 ? H[q1 * m + p2] : (Real)0;
         const Real d = (r1 && r2) ? H[q1 * m + q2] : (Real)0;
-        Real o00 = a, o01 = b, o10 = cc, o11 = d;
-        if (r_act[k1]) {                                  // rows
-          const Real c1 = r_c[k1], s1 = r_s[k1];
-          o00 = c1 * a - s1 * cc; o01 = c1 * b - s1 * d;
-          o10 = s1 * a + c1 * cc; o11 = s1 * b + c1 * d;
-        }
-        if (r_act[k2]) {                                  // columns
-          const Real c2 = r_c[k2], s2 = r_s[k2];
-          const Real x0 = o00, x1 = o10;
-          o00 = c2 * x0 - s2 * o01; o01 = s2 * x0 + c2 * o01;
-          o10 = c2 * x1 - s2 * o11; o11 = s2 * x1 + c2 * o11;
-        }
-        Hn[p1 * m + p2] = o00;
-        if (r2) Hn[p1 * m + q2] = o01;
-        if (r1) Hn[q1 * m + p2] = o10;
-        if (r1 && r2) Hn[q1 * m + q2] = o11;
+        // rows (pair k1), then columns (pair k2)
+        const Real o00 = c1 * a - s1 * cc, o01 = c1 * b - s1 * d;
+        const Real o10 = s1 * a + c1 * cc, o11 = s1 * b + c1 * d;
+        Hn[p1 * m + p2] = c2 * o00 - s2 * o01;
+        if (r2) Hn[p1 * m + q2] = s2 * o00 + c2 * o01;
+        if (r1) Hn[q1 * m + p2] = c2 * o10 - s2 * o11;
+        if (r1 && r2) Hn[q1 * m + q2] = s2 * o10 + c2 * o11;
       } else {
         const int f = e - nblk, k = __float2int_rd(((float)f + 0.5f) * inv_m), i = f - k * m;
-        if (!r_act[k]) continue;
-        const int p = r_p[k], q = r_q[k];
+        int p, q;
+        jacobi_pair(t, k, nr, p, q);
+        if (q >= m) continue;
         const Real c = r_c[k], s = r_s[k];
         const Real vp = V[i * m + p], vq = V[i * m + q];
         V[i * m + p] = c * vp - s * vq;
@@ -244,81 +247,65 @@ static __device__ void jacobi_eig(double* H, double* V, int m, double* W1, doubl
   }
 }
 
-// Q[:, j] for one row i from L q^T = z^T (forward substitution), with the
-// unknowns of the row in registers: MB bounds m at compile time so that the
-// loops unroll (a runtime-sized array would live in local memory).
-template <int MB>
-static __device__ void fwd_subst(const float* Z, float* Q, int I, int m, const float* Lf) {
+// These routines run a handful of times per call, so their code is kept
+// compact (loops, not full unrolls: straight-line code executed once is bound
+// by instruction fetch), with eight-wide register batches so that the loads
+// of a batch are in flight together.
+
+// Q = Z L^{-T} (Q[:, j] of row i from L q^T = z^T, forward substitution), one
+// thread per row, the row's unknowns read back from Q; dinv[j] = 1 / L_jj.
+static __device__ void fwd_subst(const float* Z, float* Q, int I, int m, const float* Lf, const float* dinv) {
   for (int i = threadIdx.x; i < I; i += blockDim.x) {
-    float q[MB];
+    for (int j = 0; j < m; ++j) {
+      float t = Z[j * I + i];
+      for (int k0 = 0; k0 < j; k0 += 8) {
+        float lv[8], qv[8];
 #pragma unroll
-    for (int j = 0; j < MB; ++j) {
-      if (j < m) {
-        float t = Z[j * I + i];
+        for (int u = 0; u < 8; ++u) {
+          const bool in = k0 + u < j;
+          lv[u] = in ? Lf[j * m + k0 + u] : 0.f;
+          qv[u] = in ? Q[(k0 + u) * I + i] : 0.f;
+        }
 #pragma unroll
-        for (int k = 0; k < j; ++k) t = fmaf(-Lf[j * m + k], q[k], t);
-        q[j] = t / Lf[j * m + j];
-        Q[j * I + i] = q[j];
+        for (int u = 0; u < 8; ++u) t = fmaf(-lv[u], qv[u], t);
       }
+      Q[j * I + i] = t * dinv[j];
     }
   }
 }
 
-// Right-looking Cholesky of the symmetric m x m matrix in Lf (m <= MB <= 32)
-// by one warp: lane i keeps row i of the running Schur complement in
-// registers; step j broadcasts the pivot and the scaled column j by shuffles
-// and updates every later entry of the row.  On exit the lower triangle of Lf
-// holds L; `bad` gets the first column whose pivot is not above 1e-5 (the
-// factor is then incomplete and not written).
-template <int MB>
-static __device__ void chol_warp(float* Lf, int m, int lane, int& bad) {
-  float row[MB];
-#pragma unroll
-  for (int k = 0; k < MB; ++k) row[k] = (lane < m && k < m) ? Lf[lane * m + k] : 0.f;
-  int fail = -1;
-#pragma unroll
-  for (int j = 0; j < MB; ++j) {
-    if (j < m && fail < 0) {
-      const float piv = __shfl_sync(0xffffffffu, row[j], j);
-      if (!(piv > 1e-5f)) {
-        fail = j;
-      } else {
-        const float ljj = sqrtf(piv);
-        const float lij = lane > j ? row[j] / ljj : (lane == j ? ljj : 0.f);
-        row[j] = lij;
-#pragma unroll
-        for (int k = j + 1; k < MB; ++k) row[k] = fmaf(-lij, __shfl_sync(0xffffffffu, lij, k), row[k]);
-      }
-    }
-  }
-  if (fail >= 0) {
-    if (lane == 0) bad = fail;
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < MB; ++k)
-    if (k <= lane && lane < m) Lf[lane * m + k] = row[k];
-}
-
-// Left-looking Cholesky by one warp for m > 32 (same contract as chol_warp).
-static __device__ void chol_warp_left(float* Lf, int m, int lane, int& bad) {
+// Right-looking Cholesky C = L L^T of the symmetric m x m matrix in Lf
+// (row-major) by one warp in shared memory: step j takes the pivot, scales
+// column j below it (one row per lane) and updates the trailing lower
+// triangle, lane i row i.  On exit the lower triangle of Lf holds L and
+// dinv[j] = 1 / L_jj; `bad` gets the first column whose pivot is not above
+// 1e-5 (the factor is then incomplete).
+static __device__ void chol_warp(float* Lf, float* dinv, int m, int lane, int& bad) {
   for (int j = 0; j < m; ++j) {
-    float s = 0.f;
-    for (int k = lane; k < j; k += 32) s = fmaf(Lf[j * m + k], Lf[j * m + k], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float piv = Lf[j * m + j] - s;
-    __syncwarp();
-    if (!(piv > 1e-5f)) { if (lane == 0) bad = j; return; }
-    const float ljj = sqrtf(piv);
-    const float inv = 1.f / ljj;
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      float t = Lf[i * m + j];
-      for (int k = 0; k < j; ++k) t = fmaf(-Lf[i * m + k], Lf[j * m + k], t);
-      Lf[i * m + j] = t * inv;
+    const float piv = Lf[j * m + j];
+    if (!(piv > 1e-5f)) {
+      if (lane == 0) bad = j;
+      return;
     }
+    const float ljj = sqrtf(piv), inv = 1.f / ljj;
+    for (int i = j + 1 + lane; i < m; i += 32) Lf[i * m + j] *= inv;
     __syncwarp();
-    if (lane == 0) Lf[j * m + j] = ljj;
+    if (lane == 0) { Lf[j * m + j] = ljj; dinv[j] = inv; }
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const float lij = Lf[i * m + j];
+      for (int k0 = j + 1; k0 <= i; k0 += 8) {
+        float lk[8], cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool in = k0 + u <= i;
+          lk[u] = in ? Lf[(k0 + u) * m + j] : 0.f;
+          cv[u] = in ? Lf[i * m + k0 + u] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (k0 + u <= i) Lf[i * m + k0 + u] = fmaf(-lij, lk[u], cv[u]);
+      }
+    }
     __syncwarp();
   }
 }
@@ -327,10 +314,9 @@ static __device__ void chol_warp_left(float* Lf, int m, int lane, int& bad) {
 // Cholesky QR on column-normalised Z (FP32; C = Z^T Z has unit diagonal, and
 // a pivot below 1e-5 marks a column as dependent on the previous ones).
 // Dependent columns are replaced by pseudo-random +-1 vectors and the
-// factorisation is repeated.  Warp-parallel dots; Cholesky by warp 0
-// (right-looking in registers up to m = 32);
-// row-wise forward substitution.  Returns false if it did not succeed.
-template <int MMAX>
+// factorisation is repeated.  Warp-parallel dots; Cholesky by warp 0 in
+// shared memory; row-wise forward substitution.  Cf: m floats of scratch
+// (the column scales, then 1 / L_jj).  Returns false if it did not succeed.
 static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float* Cf, uint64_t seed, int salt) {
   __shared__ int bad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -376,12 +362,8 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
     }
     if (threadIdx.x == 0) bad = -1;
     __syncthreads();
-    // Cholesky C = L L^T by warp 0, L in the lower triangle of Lf
-    if (warp == 0) {
-      if (m <= 16) chol_warp<16>(Lf, m, lane, bad);
-      else if (m <= 32) chol_warp<32>(Lf, m, lane, bad);
-      else chol_warp_left(Lf, m, lane, bad);
-    }
+    // Cholesky C = L L^T by warp 0, L in the lower triangle of Lf, 1 / L_jj in Cf
+    if (warp == 0) chol_warp(Lf, Cf, m, lane, bad);
     __syncthreads();
     if (bad >= 0) {
       const int from = bad;
@@ -395,10 +377,7 @@ static __device__ bool cholqr(float* Z, float* Q, int I, int m, float* Lf, float
       continue;
     }
     // Q = Z L^{-T}: row-wise forward substitution L q^T = z^T
-    if (m <= 16) fwd_subst<16>(Z, Q, I, m, Lf);
-    else if constexpr (MMAX <= 32) fwd_subst<32>(Z, Q, I, m, Lf);
-    else if (m <= 32) fwd_subst<32>(Z, Q, I, m, Lf);
-    else fwd_subst<kMaxM>(Z, Q, I, m, Lf);
+    fwd_subst(Z, Q, I, m, Lf, Cf);
     __syncthreads();
     return true;
   }
@@ -567,10 +546,10 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     gram_times<(MMAX > 32)>(G, Q, Z, Qt, I, m);
     double prev = -1.0;
     for (int it = 0; it < 30; ++it) {
-      cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, it);
+      cholqr(Z, Q, I, m, Lf, Cf, a.seed, it);
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) Z[e] = Q[e];
       __syncthreads();
-      cholqr<MMAX>(Z, Q, I, m, Lf, Cf, a.seed, 1000 + it);
+      cholqr(Z, Q, I, m, Lf, Cf, a.seed, 1000 + it);
       gram_times<(MMAX > 32)>(G, Q, Z, Qt, I, m);
       float vf[1] = {0.f};
       for (int e = threadIdx.x; e < I * m; e += blockDim.x) vf[0] = fmaf(Q[e], Z[e], vf[0]);
@@ -623,17 +602,18 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
   __syncthreads();
   // truncation rank (Algorithm "Compression"): smallest i in 1..P with
   // sum_{r>i} sigma_r^2 / sum_{r<=P} sigma_r^2 < mlsvd_tol / L
+  // (the tails by one backward pass: tail_i = tail_{i+1} + sigma_{i+1}^2)
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int r = 0; r < P; ++r) tot += fabs((double)lam[order[r]]);
+    double* tail = red;                         // P + 1 <= 128 doubles, free here
+    tail[P] = 0.0;
+    for (int r = P - 1; r >= 0; --r) tail[r] = tail[r + 1] + fabs((double)lam[order[r]]);
+    const double tot = tail[0];
     int rk = P;
     if (tot <= 0.0) rk = 1;
     else {
-      for (int i = 1; i <= P; ++i) {
-        double tail = 0.0;
-        for (int r = i; r < P; ++r) tail += fabs((double)lam[order[r]]);
-        if (tail / tot < a.mlsvd_tol / a.L) { rk = i; break; }
-      }
+      const double lim = tot * (a.mlsvd_tol / a.L);
+      for (int i = 1; i <= P; ++i)
+        if (tail[i] < lim) { rk = i; break; }
     }
     *a.rank_out = rk;
   }

@@ -149,8 +149,14 @@ __host__ __device__ inline size_t batch_compress_smem(int dmax, int Rmax) {
          eig_smem_bytes(dmax, P, false, false);
 }
 
+// Resident blocks per SM the register allocation must allow (170 registers a
+// thread for 64- and 128-thread blocks); without the bound the allocator
+// caps registers for an occupancy target of its own and spills.
 template <int TH>
-__global__ void __launch_bounds__(TH) k_batch(BatchArgs a, int dmax, int Rmax, size_t smem_bytes) {
+constexpr int kBatchMinBlocks = TH == 64 ? 6 : TH == 128 ? 3 : 1;
+
+template <int TH>
+__global__ void __launch_bounds__(TH, kBatchMinBlocks<TH>) k_batch(BatchArgs a, int dmax, int Rmax, size_t smem_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_idx;
   __shared__ int s_rank[3];

@@ -104,7 +104,7 @@ size_t eig_work_floats(int I, int P) {
   return (size_t)I * I + 64;
 }
 
-__global__ void __launch_bounds__(kEigThreads) k_eig(EigArgs a) {
+__global__ void __launch_bounds__(kEigThreads, 1) k_eig(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   eig_run(a, smem_raw);
 }

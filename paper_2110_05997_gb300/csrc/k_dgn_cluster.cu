@@ -104,23 +104,24 @@ __device__ inline void carve_cluster(const Shape& s, Bufs& b, ClusterBufs& c, un
   b.F = nullptr; b.Kb = nullptr; b.Bb = nullptr;
 }
 
-// Indices (i_2, ..., i_L) of global fibre F of the core (F = i_2 + I_2 (i_3 + ...)).
+// Indices (i_2, ..., i_L) of global fibre F of the core (F = i_2 + I_2 (i_3 + ...)),
+// in 32-bit arithmetic (a core that fits the cluster has far fewer than 2^31 fibres).
 template <int L>
 __device__ __forceinline__ void core_fibre(const Shape& s, long long F, int (&il)[kMaxL]) {
-  long long rem = F;
+  unsigned rem = (unsigned)F;
 #pragma unroll
   for (int l = 1; l < L; ++l) {
-    const long long q = rem / s.d[l];
-    il[l] = (int)(rem - q * s.d[l]);
+    const unsigned d = (unsigned)s.d[l], q = rem / d;
+    il[l] = (int)(rem - q * d);
     rem = q;
   }
 }
 
 // Residual and gradient of the cluster's core: this CTA's slice [fa, fb) of
 // fibres gives fsq and the partial gradient; after a cluster barrier every
-// CTA sums all partials in rank order into b.G (and fsq), and ginf = ||G||_inf.
-// The caller must pass a cluster barrier before the next call (the partials
-// are overwritten).
+// CTA sums all partials in rank order into b.G (and fsq, in every thread),
+// and ginf = ||G||_inf (in thread 0).  The caller must pass a cluster barrier
+// before the next call (the partials are overwritten).
 template <int L>
 __device__ void core_pass_cluster(const Shape& s, const Bufs& b, const ClusterBufs& c, long long fa, long long fb,
                                   double& fsq, double& ginf, double* s_fsq) {
@@ -150,8 +151,8 @@ __device__ void core_pass_cluster(const Shape& s, const Bufs& b, const ClusterBu
     c.Es[e] = ev;
     accf[0] = fmaf(ev, ev, accf[0]);
   }
-  double acc[1];
-  block_sum<1>(accf, acc, b.red);              // contains the barriers that publish Es
+  float acc[1];
+  block_sum_f<1>(accf, acc, b.red);            // contains the barriers that publish Es
   // (3) mode-1 gradient G1[i, r] = sum_f e[i, f] kr[f, r] (the fibres split in
   // `parts` ranges, one thread per (i, r, range), partial sums added) and q_f = e_f^T W1
   const int parts = (int)blockDim.x / (d0 * R) > 1 ? (int)blockDim.x / (d0 * R) : 1;
@@ -204,7 +205,7 @@ __device__ void core_pass_cluster(const Shape& s, const Bufs& b, const ClusterBu
       }
     }
   }
-  if (threadIdx.x == 0) *s_fsq = acc[0];
+  if (threadIdx.x == 0) *s_fsq = (double)acc[0];
   // (5) the cluster's sum, in rank order, into every CTA
   cl_sync();
   const uint32_t cs = cl_size();
@@ -215,10 +216,18 @@ __device__ void core_pass_cluster(const Shape& s, const Bufs& b, const ClusterBu
     b.G[j] = g;
     gm = fmaxf(gm, fabsf(g));
   }
-  double fs = 0.0;
-  for (uint32_t rk = 0; rk < cs; ++rk) fs += cl_ldd(cl_map(s_fsq, rk));
-  fsq = fs;
-  ginf = (double)block_max(gm, b.red);         // also publishes b.G
+  // fsq: the partials summed in rank order by thread 0 only (FP64), then
+  // published to every thread by block_max's barriers
+  __shared__ double s_total;
+  if (threadIdx.x == 0) {
+    double fs = 0.0;
+    for (uint32_t rk = 0; rk < cs; ++rk) fs += cl_ldd(cl_map(s_fsq, rk));
+    s_total = fs;
+  }
+  const float gmax = block_max(gm, b.red);     // also publishes b.G and s_total
+  fsq = s_total;
+  ginf = 0.0;
+  if (threadIdx.x == 0) ginf = (double)gmax;
 }
 
 template <int L>
@@ -281,7 +290,9 @@ __global__ void __launch_bounds__(1024) k_dgn_cluster(DgnArgs a) {
   const bool bad0 = !isfinite(fsq);
   for (int k = 1; k <= a.maxiter && !bad0; ++k) {
     const double mu = st.mu;
-    if (threadIdx.x == 0) s_maxit = cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
+    // the table rank 0 filled is visible to the cluster after the prologue's barrier
+    if (threadIdx.x == 0)
+      s_maxit = (a.k0 + k <= a.cgtab_len) ? a.cgtab[a.k0 + k] : cg_maxiter(a.k0 + k, a.seed, a.cg_a, a.cg_b);
     grams_pi<L>(s, b);                           // its first barrier publishes s_maxit
     if (a.precond) regularize_block<L>(s, b, mu);
     else regularize<L>(s, b, mu);

@@ -268,11 +268,17 @@ __device__ __forceinline__ float hv_entry(const Shape& s, const Bufs& b, const f
   return z;
 }
 
+// The CG stop test ||r||^2 < tol in FP32: the smallest float >= tol (rounded
+// up), so that rr < tolf exactly when (double)rr < tol, with one conversion
+// per call instead of an FP64 compare per thread and iteration.
+__device__ __forceinline__ float stop_threshold_f(double tol) { return __double2float_ru(tol); }
+
 // Algorithm "Conjugate gradient - dGN" (Sec. 4.1.3) on
 // B = M^{-1/2}(J^T J + mu D)M^{-1/2}, x0 = 0, r0 = M^{-1/2} A^T b, stop on
 // ||r||^2 < tol or maxit; x_hat is left in b.X.  Returns the iterations run.
 template <int L>
 __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const float tolf = stop_threshold_f(tol);
   // The inner products are FP32 block sums; alpha and beta are FP32 quotients
   // of them (the updates use FP32 alpha and beta, and the correctly rounded
   // FP32 quotient is what an FP64 quotient rounded to FP32 gives, barring
@@ -325,7 +331,7 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
       b.Tmp[j] = b.msq[l * R + r] * pv;
     }
     __syncthreads();
-    if ((double)rr < tol) break;
+    if (rr < tolf) break;
   }
   return its;
 }
@@ -338,6 +344,7 @@ __device__ int pcg(const Shape& s, const Bufs& b, double mu, int maxit, double t
 // variables (msq = 1).  Returns the iterations run.
 template <int L>
 __device__ int pcg_block(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const float tolf = stop_threshold_f(tol);
   const int n = s.n, R = s.R, RR = R * R;
   auto minv = [&](int j, const float* v) {          // (V^(l) Minv_l)[i, r] for entry j = (l, i, r)
     int l, i, r; decode_j<L>(s, j, l, i, r);
@@ -392,7 +399,7 @@ __device__ int pcg_block(const Shape& s, const Bufs& b, double mu, int maxit, do
     its = it + 1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) b.P[j] = fmaf(bf, b.P[j], b.Tmp[j]);
     __syncthreads();
-    if ((double)rz < tol) break;
+    if (rz < tolf) break;
   }
   return its;
 }
@@ -407,6 +414,7 @@ __device__ int pcg_block(const Shape& s, const Bufs& b, double mu, int maxit, do
 // step on the full tensor).
 template <int L, int RP>
 __device__ int pcg_rows(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const float tolf = stop_threshold_f(tol);
   const int n = s.n, R = s.R, RR = R * R;
   int nrows = 0;
 #pragma unroll
@@ -481,7 +489,7 @@ __device__ int pcg_rows(const Shape& s, const Bufs& b, double mu, int maxit, dou
       b.Tmp[j] = b.msq[l * R + r] * pv;
     }
     __syncthreads();
-    if ((double)rr < tol) break;
+    if (rr < tolf) break;
   }
   return its;
 }
@@ -493,6 +501,7 @@ __device__ int pcg_rows(const Shape& s, const Bufs& b, double mu, int maxit, dou
 // (FP32 scalars as described there).
 template <int L>
 __device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, double tol) {
+  const float tolf = stop_threshold_f(tol);
   const int n = s.n, R = s.R;
   const int j = threadIdx.x;
   const bool own = j < n;
@@ -541,7 +550,7 @@ __device__ int pcg_owned(const Shape& s, const Bufs& b, double mu, int maxit, do
       b.Tmp[j] = m * pj;
     }
     __syncthreads();
-    if ((double)rr < tol) break;
+    if (rr < tolf) break;
   }
   if (own) b.X[j] = x;
   __syncthreads();
@@ -581,8 +590,8 @@ __device__ void balance(const Shape& s, const Bufs& b) {
 }
 
 // After the PCG: x = M^{-1/2} x_hat (into b.X), the predicted decrease
-// F - ½||f + Jx||^2 = <g, x> - ½<x, J^T J x> (g = A^T b), the squared step
-// norm ||x||^2, then w += x and balancing.
+// F - ½||f + Jx||^2 = <g, x> - ½<x, J^T J x> (g = A^T b) and the squared step
+// norm ||x||^2 (both in thread 0), then w += x and balancing.
 template <int L>
 __device__ void finish_step(const Shape& s, const Bufs& b, double& pred_drop, double& step) {
   const int R = s.R;
@@ -600,17 +609,23 @@ __device__ void finish_step(const Shape& s, const Bufs& b, double& pred_drop, do
     vf[1] = fmaf(x, hv_entry<L>(s, b, b.X, l, i, r), vf[1]);
     vf[2] = fmaf(x, x, vf[2]);
   }
-  double v[3];
-  block_sum<3>(vf, v, b.red);
-  pred_drop = v[0] - 0.5 * v[1];
-  step = v[2];                      // squared here; the caller's bookkeeping thread takes the root
+  float v[3];
+  block_sum_f<3>(vf, v, b.red);
+  // FP64 only in thread 0, the callers' bookkeeping thread (the FP64 pipe is
+  // too slow for a conversion in every thread); other threads get 0
+  pred_drop = 0.0; step = 0.0;
+  if (threadIdx.x == 0) {
+    pred_drop = (double)v[0] - 0.5 * (double)v[1];
+    step = (double)v[2];            // squared here; the caller takes the root
+  }
   for (int j = threadIdx.x; j < s.n; j += blockDim.x) b.W[j] += b.X[j];
   __syncthreads();
   balance<L>(s, b);
 }
 
 // Residual and gradient of a tensor held by the CTA (Sec. 4.1.3 "Computing the
-// residual", "Computing the gradient"): f = S - [[W]], fsq = ||f||^2 in FP64,
+// residual", "Computing the gradient"): f = S - [[W]], fsq = ||f||^2 (FP32
+// block sum) and ginf = ||G||_inf, both returned in thread 0 (0 elsewhere),
 // G = A^T b = -grad F, blockwise f_(l) (Khatri-Rao of the other factors).
 // The MTTKRPs share two contractions of f: over the last mode (serving modes
 // 1..L-1) and over the first mode (serving mode L).
@@ -642,9 +657,9 @@ __device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& gi
     b.F[e] = f;
     accf[0] = fmaf(f, f, accf[0]);
   }
-  double acc[1];
-  block_sum<1>(accf, acc, b.red);
-  fsq = acc[0];
+  float acc[1];
+  block_sum_f<1>(accf, acc, b.red);
+  fsq = threadIdx.x == 0 ? (double)acc[0] : 0.0;   // valid in thread 0 (see the end)
   // A[r][e'] = sum_{iL} f[e', iL] W_L[iL, r];  B[r][e''] = sum_{i0} f[i0, e''] W_0[i0, r]
   for (int q = threadIdx.x; q < R * NL; q += blockDim.x) {
     const int r = q / NL, e = q - r * NL;
@@ -702,7 +717,9 @@ __device__ void core_pass(const Shape& s, const Bufs& b, double& fsq, double& gi
     b.G[j] = g;
     gm = fmaxf(gm, fabsf(g));
   }
-  ginf = (double)block_max(gm, b.red);
+  const float gmax = block_max(gm, b.red);
+  ginf = 0.0;
+  if (threadIdx.x == 0) ginf = (double)gmax;
 }
 
 // Stop tests of Sec. 4.1.3 in the printed order (reading: windows as printed,
