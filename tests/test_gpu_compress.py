@@ -109,13 +109,18 @@ def _tensor_core_pass(dims, R):
 # every padded rank of the CUDA-core pass (8, 12, 16, 32, 64), one to four rows
 # per thread (I1 up to 1024), orders 3 and 4, ragged last batches of fibres; on
 # the tensor-core pass one and two row chunks (I1 = 200, 128, 256), a rank of
-# one, fewer fibres than one tile and ragged last tiles
+# one, fewer fibres than one tile, ragged last tiles, and runs of I2 fibres
+# (fixed i3..iL) shorter than a 128-fibre tile (I2 = 3 .. 100), as long (128)
+# and longer (129, 200, 300)
 @pytest.mark.parametrize("dims,R", [((50, 40, 30), 4), ((20, 18, 16, 14), 3), ((257, 3, 5), 2), ((7, 33, 65), 6),
                                     ((300, 20, 10), 10), ((200, 17, 9), 12), ((40, 30, 20), 16),
                                     ((64, 9, 7), 20), ((33, 10, 6), 40), ((600, 5, 4), 3),
                                     ((1024, 3, 3), 16), ((20, 18, 16, 14), 12), ((130, 7, 5, 3), 30),
                                     ((100, 9, 7, 5), 15), ((128, 20, 10), 8), ((256, 12, 11), 16),
-                                    ((4, 50, 3), 1), ((40, 3, 2), 5), ((100, 60, 50), 15)])
+                                    ((4, 50, 3), 1), ((40, 3, 2), 5), ((100, 60, 50), 15),
+                                    ((100, 100, 7), 15), ((32, 100, 6, 5), 7), ((100, 64, 9), 8),
+                                    ((20, 128, 3, 2), 4), ((48, 200, 5), 10), ((24, 129, 4), 6),
+                                    ((16, 300, 3, 2), 5)])
 def test_refine_eval_matches_oracle(cpd, dims, R):
     g = np.random.default_rng(sum(dims) + R)
     T = g.standard_normal(dims).astype(np.float32).astype(np.float64)
