@@ -57,6 +57,20 @@ bool uncompressed_fits(int L, const int64_t* dims) {
   return N <= (double)(0x7fffffff - 1024);
 }
 
+// dGN with every iteration one pass over T (Sec. 4.9: uncompressed CPDs of
+// large tensors): no compression, an FP32 tensor of at least 2^20 entries,
+// a random or given start, and a shape the refinement pass covers.  The
+// single-CTA and cluster solvers hold T (or its slices) in shared memory and
+// stay the path for smaller tensors and for the MLSVD-energy start.
+constexpr double kFullMinEntries = 1048576.0;
+bool full_mode(int L, const int64_t* dims, int R, const cpd_options& o, int dtype) {
+  if (o.compress || dtype != CPD_F32) return false;
+  if (o.init != CPD_INIT_RANDOM && o.init != CPD_INIT_GIVEN) return false;
+  double N = 1.0;
+  for (int l = 0; l < L; ++l) N *= (double)dims[l];
+  return N >= kFullMinEntries && pass_ok(L, dims, R);
+}
+
 int validate_options(const cpd_options* o) {
   if (o == nullptr) return CPD_OK;
   if (o->maxiter < 1 || o->maxiter > 100000) return CPD_ERR_INVALID_ARG;
@@ -89,6 +103,7 @@ size_t smem_limit() {
 // Everything the solve needs, carved from the workspace (or sized when base == nullptr).
 struct SolvePlan {
   int L, R, dtype;
+  int full = 0;                 // every dGN iteration a pass over T (full_mode)
   long long dims[CPD_MAX_ORDER];
   int idims[CPD_MAX_ORDER];
   int P[CPD_MAX_ORDER];
@@ -127,13 +142,13 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
   p.cgtab = c.take<int>((size_t)p.cgtab_len + 1);
   Shape sc; make_shape(sc, L, cmax, R);
   p.W_core = c.take<float>(sc.n);
-  size_t smem_big = dgn_smem_bytes_host(L, cmax, R, 1, o.precond);
+  size_t smem_big = p.full ? 0 : dgn_smem_bytes_host(L, cmax, R, 1, o.precond);
   p.big_in_smem = smem_big <= smem_limit() ? 1 : 0;
-  p.dgn_smem = dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond);
+  p.dgn_smem = p.full ? 0 : dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond);
   if (!p.big_in_smem) p.gscratch = c.take<float>(dgn_gscratch_floats_host(L, cmax, R));
   // a core of 8192 entries or more (or one beyond a CTA's shared memory) is
   // solved by a cluster, each CTA holding a slice of it (FP32 tensors only)
-  if ((sc.N >= 8192 || !p.big_in_smem) && (o.compress || p.dtype == CPD_F32)) {
+  if (!p.full && (sc.N >= 8192 || !p.big_in_smem) && (o.compress || p.dtype == CPD_F32)) {
     for (int cs : {16, 8}) {
       const size_t sm = dgn_cluster_smem_bytes_host(L, cmax, R, cs, o.precond);
       if (sm <= smem_limit() && sc.N / cmax[0] >= cs) { p.cluster = cs; p.cluster_smem = sm; break; }
@@ -172,12 +187,13 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
       p.tc_scratch = c.take<float>((p.tc_scratch_bytes + 3) / 4);
     }
   }
-  if (o.refine_maxiter > 0) {
+  if (o.refine_maxiter > 0 || p.full) {
     p.rstate = reinterpret_cast<RefineState*>(c.take<char>(refine_state_bytes()));
     p.rdone = c.take<int>(1);
     p.resq = c.take<double>(2);
     p.rG = c.take<float>(p.n_full);
-    p.rhist = c.take<double>((size_t)o.refine_maxiter + 1);
+    const int hmax = p.full && o.maxiter > o.refine_maxiter ? o.maxiter : o.refine_maxiter;
+    p.rhist = c.take<double>((size_t)hmax + 1);
     size_t sm = refine_step_smem_bytes(L, p.dims, R, 1, o.precond);
     p.r_vec_in_smem = sm <= smem_limit() ? 1 : 0;
     p.r_smem = refine_step_smem_bytes(L, p.dims, R, p.r_vec_in_smem, o.precond);
@@ -362,6 +378,29 @@ int enqueue_solve(SolvePlan& p, const cpd_options& o, const void* T, int dtype, 
   const int trace_cap = trace ? (o.maxiter + o.refine_maxiter) : 0;
   CK(cudaMemsetAsync(p.err, 0, sizeof(int), st));
 
+  if (p.full) {
+    // dGN on T itself, every iteration one pass (no core solve): the start
+    // (random draws or the given factors, balanced) and mu0 = tau mean|T|,
+    // then the iterations, then (refine_maxiter > 0) the refinement as the
+    // method states it, a second run of iterations from where dGN stopped
+    PL("full_start", launch_full_start(L, p.dims, R, o.init, W0, o.seed, o.tau, static_cast<const float*>(T),
+                                       p.resq, p.W_full, p.res, p.cgtab, p.cgtab_len, o.cg_a, o.cg_b, st));
+    PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
+    const bool second = o.refine_maxiter > 0;
+    int rc = enqueue_refine(p, o, T, L, R, p.W_full, o.maxiter, 0, p.cgtab_len, trace, trace_cap, st,
+                            second ? nullptr : side, second ? nullptr : refine_loop);
+    if (rc != CPD_OK) return rc;
+    PL("refine_result", launch_refine_result(p.rstate, p.res, st));
+    if (second) {
+      PL("refine_init", launch_refine_init(p.rstate, p.res, p.rdone, st));
+      rc = enqueue_refine(p, o, T, L, R, p.W_full, o.refine_maxiter, o.maxiter, p.cgtab_len, trace, trace_cap, st,
+                          nullptr, nullptr);
+      if (rc != CPD_OK) return rc;
+    }
+    PL("normalize", launch_normalize(L, p.dims, R, p.W_full, W_out, lambda_out, st));
+    return CPD_OK;
+  }
+
   // ---- compression and initial factors -----------------------------------------
   DgnArgs a{};
   a.R = R;
@@ -501,14 +540,22 @@ size_t cpd_workspace_size(int L, const int64_t* dims, int R, const cpd_options* 
   if (validate_common(L, dims, R) != CPD_OK) return 0;
   cpd_options o; cpd_default_options(&o);
   if (opts) o = *opts;
-  if (!o.compress && !uncompressed_fits(L, dims)) return 0;
-  SolvePlan p; fill_dims(p, L, dims, R); p.dtype = CPD_F32;
+  const bool full = full_mode(L, dims, R, o, CPD_F32);
+  if (!o.compress && !full && !uncompressed_fits(L, dims)) return 0;
+  SolvePlan p; fill_dims(p, L, dims, R); p.dtype = CPD_F32; p.full = full ? 1 : 0;
   Carver c(nullptr, 0);
   plan_solve(p, c, o);
+  if (full && uncompressed_fits(L, dims)) {     // an FP64 tensor of this shape takes the other path
+    SolvePlan q; fill_dims(q, L, dims, R); q.dtype = CPD_F64;
+    Carver c2(nullptr, 0);
+    plan_solve(q, c2, o);
+    if (c2.used > c.used) c.used = c2.used;
+  }
   // component calls reuse the same workspace: make room for their scratch too
   int d[CPD_MAX_ORDER] = {1, 1, 1, 1};
   for (int l = 0; l < L; ++l) d[l] = (int)dims[l];
-  size_t extra = (dgn_smem_bytes_host(L, d, R, 1) <= smem_limit()) ? 0 : dgn_gscratch_floats_host(L, d, R) * 4;
+  size_t extra = (!uncompressed_fits(L, dims) || dgn_smem_bytes_host(L, d, R, 1) <= smem_limit())
+                     ? 0 : dgn_gscratch_floats_host(L, d, R) * 4;
   size_t need = c.used + 256;
   return need > extra + 512 ? need : extra + 512;
 }
@@ -531,9 +578,10 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     return CPD_ERR_UNSUPPORTED;
   if (o.refine_maxiter > 0 && !pass_ok(L, dims, R)) return CPD_ERR_UNSUPPORTED;
   if (o.precond == CPD_PRECOND_BLOCK && R > 32) return CPD_ERR_UNSUPPORTED;
-  if (!o.compress && !uncompressed_fits(L, dims)) return CPD_ERR_UNSUPPORTED;
+  const bool full = full_mode(L, dims, R, o, dtype);
+  if (!o.compress && !full && !uncompressed_fits(L, dims)) return CPD_ERR_UNSUPPORTED;
 
-  SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype;
+  SolvePlan p; fill_dims(p, L, dims, R); p.dtype = dtype; p.full = full ? 1 : 0;
   Carver c(workspace, ws_bytes);
   plan_solve(p, c, o);
   if (!c.ok) return CPD_ERR_WORKSPACE;
@@ -564,7 +612,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     }
     if (exec == nullptr) {
       cudaGraph_t g = nullptr;
-      cudaStream_t side = o.refine_maxiter > 0 ? side_stream() : nullptr;
+      cudaStream_t side = (o.refine_maxiter > 0 || full) ? side_stream() : nullptr;
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         const long long before = cpd_launch_count();
         const int rc = enqueue_solve(p, o, T, dtype, L, R, W0, W_out, lambda_out, trace, st, side, &loop);
@@ -610,7 +658,7 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
     int core_dims[CPD_MAX_ORDER] = {0, 0, 0, 0};
     if (o.compress) CK(cudaMemcpyAsync(core_dims, p.core_dims_dev, sizeof(int) * CPD_MAX_ORDER, cudaMemcpyDeviceToHost, st));
     int r_iters = 0, r_stop = 0, r_cg = 0, r_status = CPD_OK, r_steps = 0; double r_err = 0.0, r_mu = 0.0;
-    if (o.refine_maxiter > 0)
+    if (o.refine_maxiter > 0 || full)
       CK(read_refine_result(p.rstate, &r_iters, &r_stop, &r_cg, &r_err, &r_mu, &r_status, &r_steps, st));
     CK(cudaStreamSynchronize(st));
     // a replayed loop body ran max(0, steps - 1) times (the first step is

@@ -231,11 +231,14 @@ __global__ void k_abs_sum(const float* T, long long N, double* out) {
 
 // The starting factors on the full tensor (Sec. 4.1.2: random N(0,1) draws of
 // the same SplitMix64 stream as the core solver, or the caller's), balanced
-// (Sec. 4.1.3 "Updates"), and mu0 = tau mean|T| (Sec. 4.1.3) into the record
-// the refinement state is primed from.
+// (Sec. 4.1.3 "Updates"), mu0 = tau mean|T| (Sec. 4.1.3) into the record the
+// refinement state is primed from, and the table of CG iteration caps (the
+// core solver's prologue fills it on the compressed path).
 __global__ void __launch_bounds__(1024) k_full_start(int L, Dims4 dims, int R, int init, const float* W0,
                                                      uint64_t seed, double tau, const double* abs_sum, float* W,
-                                                     DevResult* res) {
+                                                     DevResult* res, int* cgtab, int cgtab_len, double cg_a,
+                                                     double cg_b) {
+  fill_cg_table(cgtab, cgtab_len, seed, cg_a, cg_b);
   long long off[CPD_MAX_ORDER + 1];
   off[0] = 0;
   long long N = 1;
@@ -272,8 +275,8 @@ __global__ void __launch_bounds__(1024) k_full_start(int L, Dims4 dims, int R, i
 }
 
 cudaError_t launch_full_start(int L, const long long* dims, int R, int init, const float* W0, uint64_t seed,
-                              double tau, const float* T, double* abs_sum, float* W, DevResult* res,
-                              cudaStream_t st) {
+                              double tau, const float* T, double* abs_sum, float* W, DevResult* res, int* cgtab,
+                              int cgtab_len, double cg_a, double cg_b, cudaStream_t st) {
   long long N = 1;
   Dims4 d{};
   for (int l = 0; l < CPD_MAX_ORDER; ++l) d.v[l] = l < L ? dims[l] : 1;
@@ -285,7 +288,25 @@ cudaError_t launch_full_start(int L, const long long* dims, int R, int init, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_abs_sum<<<4 * sms, 512, 0, st>>>(T, N, abs_sum);
   count_launch();
-  k_full_start<<<1, 1024, 0, st>>>(L, d, R, init, W0, seed, tau, abs_sum, W, res);
+  k_full_start<<<1, 1024, 0, st>>>(L, d, R, init, W0, seed, tau, abs_sum, W, res, cgtab, cgtab_len, cg_a, cg_b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace cpdk
+
+namespace cpdk {
+
+// The outcome of a run of pass-based iterations as the solve's result record
+// (dGN on T without compression: the iterations are the solve).
+__global__ void k_refine_result(const RefineState* s, DevResult* r) {
+  r->status = s->status; r->iters = s->iters; r->stop = s->stop; r->cg_total = s->cg_total;
+  r->kglob = s->kglob; r->pad0 = 0;
+  r->rel_err = s->rel_err; r->mu = s->mu; r->grad_inf = 0.0; r->normS = s->normT;
+}
+
+cudaError_t launch_refine_result(const RefineState* state, DevResult* res, cudaStream_t st) {
+  k_refine_result<<<1, 1, 0, st>>>(state, res);
   count_launch();
   return cudaGetLastError();
 }

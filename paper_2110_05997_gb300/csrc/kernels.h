@@ -207,12 +207,14 @@ size_t refine_step_smem_bytes(int L, const long long* dims, int R, int vec_in_sm
 cudaError_t launch_refine_step(const RefineStepArgs& a, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_refine_init(RefineState* state, const DevResult* core_res, int* done,
                                cudaStream_t st);
+// The state after a run of pass-based iterations as the solve's result record.
+cudaError_t launch_refine_result(const RefineState* state, DevResult* res, cudaStream_t st);
 // dGN on a large tensor without compression (every iteration a pass over T):
 // the balanced starting factors on T (random or given) into W and mu0 =
 // tau mean|T| into *res, from which launch_refine_init primes the state.
 cudaError_t launch_full_start(int L, const long long* dims, int R, int init, const float* W0, uint64_t seed,
-                              double tau, const float* T, double* abs_sum, float* W, DevResult* res,
-                              cudaStream_t st);
+                              double tau, const float* T, double* abs_sum, float* W, DevResult* res, int* cgtab,
+                              int cgtab_len, double cg_a, double cg_b, cudaStream_t st);
 size_t refine_state_bytes();
 cudaError_t read_refine_result(const RefineState* state, int* iters, int* stop, int* cg_total,
                                double* rel_err, double* mu, int* status, int* steps_run, cudaStream_t st);
