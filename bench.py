@@ -9,8 +9,10 @@ cores, --gram fp32 for CUDA cores), dGN on the core from the random start
 (seed 0; the MLSVD-energy start stalls on this problem in the method itself),
 uncompression, FP32 refinement iterations on T, output normalisation.
 --workload compressed200 runs the 200^3 rank-10 configuration (collinearity
-0.5, noise 1e-4, MLSVD-energy start) instead.  Metric: CPDs per second, with
-the fit of every result checked against the FP64 oracle's (within 1e-6).
+0.5, noise 1e-4, MLSVD-energy start) instead, and --workload full400 dGN
+without compression on a 400^3 rank-10 tensor (256 MB), every iteration one
+pass over T.  Metric: CPDs per second, with the fit of every result checked
+against the FP64 oracle's (within 1e-6).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -113,6 +115,10 @@ WORKLOADS = {
                    name="mlsvd_dgn_100x100x100x100_r15_noise1e-5_random_start"),
     "compressed200": dict(gen=synth.c2_compressed, opts=dict(),
                           name="mlsvd_dgn_200x200x200_r10_rho0.5_noise1e-4"),
+    # dGN without compression on a large tensor: every iteration one pass over T
+    "full400": dict(gen=lambda: dict(T=synth.planted(7, (400, 400, 400), 10, 0.0, 1e-5, np.float32)[0], R=10),
+                    opts=dict(compress=0, init="random", seed=5, gram_precision="fp32", refine_maxiter=0),
+                    name="dgn_uncompressed_400x400x400_r10_noise1e-5_random_start_seed5"),
 }
 
 
@@ -123,10 +129,18 @@ def workload(name):
 
 
 def oracle_options(extra):
+    import dataclasses
     import oracle as O
     o = dict(refine_maxiter=REFINE_MAXITER)
     o.update(extra)
-    return O.Options(**o)
+    known = {f.name for f in dataclasses.fields(O.Options)}
+    return O.Options(**{k: (bool(v) if k == "compress" else v) for k, v in o.items() if k in known})
+
+
+def solve_options(cpd, args, extra):
+    kw = dict(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram)
+    kw.update(extra)
+    return cpd.cpd_default_options(**kw)
 
 
 # sources whose kernels a stage times; a DRAM-traffic figure recorded in
@@ -336,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
     T_flat = synth.flat(T)
     Td = torch.from_numpy(T_flat).to(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    opts = cpd.cpd_default_options(refine_maxiter=REFINE_MAXITER, gram_precision=args.gram, **extra)
+    opts = solve_options(cpd, args, extra)
     ws = torch.empty(cpd.cpd_workspace_size(dims, R, opts), dtype=torch.uint8, device=dev)
 
     # timed calls read no info record (no host synchronisation inside a step);
@@ -410,7 +424,10 @@ def run_ours(args, rank, world, local_rank):
         n = v["launches"]
         if k == "refine_pass":
             # passes after the stop test exit at once: time the working ones
-            n = min(n, args.steps * (int(infos[-1].get("refine_iters", 0)) + 1))
+            passes = int(infos[-1].get("refine_iters", 0)) + 1
+            if "full_start" in prof:       # dGN without compression: its iterations are passes too
+                passes += int(infos[-1].get("iters", 0)) + 1
+            n = min(n, args.steps * passes)
         r = algorithmic(k, dims, R, infos[-1], v["ms"] / max(n, 1), pk, csum["sm_mhz"],
                         gram_bf16=(args.gram == "bf16"), sms=sms)
         r.update(traffic=measured_traffic(k), working_launches=n)
@@ -421,7 +438,8 @@ def run_ours(args, rank, world, local_rank):
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
                 config=dict(workload=wname, tensor_dims=list(dims), start=extra.get("init", "mlsvd"),
-                            rank=R, gram_precision=args.gram, refine_maxiter=REFINE_MAXITER,
+                            rank=R, gram_precision=opts.gram_precision and "bf16" or "fp32",
+                            refine_maxiter=int(opts.refine_maxiter), compress=int(opts.compress),
                             global_batch=world, parallelism=f"independent CPD per GPU x{world}",
                             l2="flushed between steps (256 MB write)", launch="cached CUDA graph per solve"),
                 e2e=e2e, gpu_launches=int(launches), roofline=roof, stage_rooflines=stage_roofs, stages=stages,
@@ -599,7 +617,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gram", choices=["fp32", "bf16"], default="bf16")
-    ap.add_argument("--workload", choices=["order4", "compressed200", "batch", "initnet"], default="order4")
+    workloads = ["order4", "compressed200", "full400", "batch", "initnet"]
+    ap.add_argument("--workload", choices=workloads, default="order4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

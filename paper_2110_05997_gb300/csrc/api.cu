@@ -142,13 +142,18 @@ void plan_solve(SolvePlan& p, Carver& c, const cpd_options& o) {
   p.cgtab = c.take<int>((size_t)p.cgtab_len + 1);
   Shape sc; make_shape(sc, L, cmax, R);
   p.W_core = c.take<float>(sc.n);
-  size_t smem_big = p.full ? 0 : dgn_smem_bytes_host(L, cmax, R, 1, o.precond);
-  p.big_in_smem = smem_big <= smem_limit() ? 1 : 0;
-  p.dgn_smem = p.full ? 0 : dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond);
-  if (!p.big_in_smem) p.gscratch = c.take<float>(dgn_gscratch_floats_host(L, cmax, R));
+  // the single-CTA solver's buffers: all in shared memory, else the
+  // tensor-sized ones in global scratch, else (high ranks) the vectors too
+  p.big_in_smem = 1;
+  if (!p.full) {
+    while (p.big_in_smem > -1 && dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond) > smem_limit())
+      --p.big_in_smem;
+    p.dgn_smem = dgn_smem_bytes_host(L, cmax, R, p.big_in_smem, o.precond);
+  }
+  if (p.big_in_smem <= 0) p.gscratch = c.take<float>(dgn_gscratch_floats_host(L, cmax, R, p.big_in_smem));
   // a core of 8192 entries or more (or one beyond a CTA's shared memory) is
   // solved by a cluster, each CTA holding a slice of it (FP32 tensors only)
-  if (!p.full && (sc.N >= 8192 || !p.big_in_smem) && (o.compress || p.dtype == CPD_F32)) {
+  if (!p.full && (sc.N >= 8192 || p.big_in_smem <= 0) && (o.compress || p.dtype == CPD_F32)) {
     for (int cs : {16, 8}) {
       const size_t sm = dgn_cluster_smem_bytes_host(L, cmax, R, cs, o.precond);
       if (sm <= smem_limit() && sc.N / cmax[0] >= cs) { p.cluster = cs; p.cluster_smem = sm; break; }
@@ -585,6 +590,9 @@ int cpd_dgn_solve(const void* T, int dtype, int L, const int64_t* dims, int R,
   Carver c(workspace, ws_bytes);
   plan_solve(p, c, o);
   if (!c.ok) return CPD_ERR_WORKSPACE;
+  // ranks whose R x R Grams and Pi matrices alone exceed a CTA's shared memory
+  if (!p.full && p.dgn_smem > smem_limit()) return CPD_ERR_UNSUPPORTED;
+  if (p.rstate && p.r_smem > smem_limit()) return CPD_ERR_UNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   // replay a captured graph of the launch sequence when the stream allows it
   bool launched = false;

@@ -11,40 +11,49 @@
 
 namespace cpdk {
 
+// big_in_smem: 1 = every buffer in shared memory; 0 = the tensor-sized ones in
+// the global scratch; -1 = the seven solver vectors there too (high ranks,
+// whose R x R Grams and Pi matrices leave no room for them).
 __host__ __device__ inline size_t dgn_smem_bytes(int L, const int* d, int R, int big_in_smem, int blk = 0) {
   Shape s; make_shape(s, L, d, R);
   size_t f = 0;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };   // 16-byte granules
   f += small_buf_floats(L, R, blk);
-  f += 7 * up((size_t)s.n);
-  if (big_in_smem) {
+  if (big_in_smem >= 0) f += 7 * up((size_t)s.n);
+  if (big_in_smem > 0) {
     const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
     f += 2 * up((size_t)s.N) + up(R * NL) + up(R * N0);
   }
   return 128 * sizeof(double) + f * sizeof(float);
 }
 
-__host__ __device__ inline size_t dgn_gscratch_floats(int L, const int* d, int R) {
+__host__ __device__ inline size_t dgn_gscratch_floats(int L, const int* d, int R, int big_in_smem = 0) {
   Shape s; make_shape(s, L, d, R);
   const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
   auto up = [](size_t x) { return (x + 63) & ~(size_t)63; };
-  return 2 * up((size_t)s.N) + up(R * NL) + up(R * N0);
+  return (big_in_smem < 0 ? 7 * up((size_t)s.n) : 0) + 2 * up((size_t)s.N) + up(R * NL) + up(R * N0);
 }
 
-// Carve the solver's buffers: small ones always in shared memory, tensor-sized
-// ones in shared memory when big_in_smem, else in the global scratch.
+// Carve the solver's buffers: small ones always in shared memory, the vectors
+// there unless big_in_smem < 0, tensor-sized ones there when big_in_smem > 0;
+// the rest in the global scratch (layout of dgn_gscratch_floats).
 __device__ inline void carve(const Shape& s, Bufs& b, unsigned char* smem, float* gscratch,
                       int big_in_smem, float** Sbuf, int blk = 0) {
   const int L = s.L, R = s.R;
   auto up = [](size_t x) { return (x + 3) & ~(size_t)3; };
+  auto up64 = [](size_t x) { return (x + 63) & ~(size_t)63; };
   b.red = reinterpret_cast<double*>(smem);
   float* p = carve_small(b, reinterpret_cast<float*>(smem + 128 * sizeof(double)), L, R, blk);
+  float* gq = gscratch;
   float** vecs[7] = {&b.W, &b.G, &b.X, &b.Rr, &b.P, &b.Z, &b.Tmp};
-  for (int v = 0; v < 7; ++v) { *vecs[v] = p; p += up((size_t)s.n); }
+  for (int v = 0; v < 7; ++v) {
+    if (big_in_smem >= 0) { *vecs[v] = p; p += up((size_t)s.n); }
+    else { *vecs[v] = gq; gq += up64((size_t)s.n); }
+  }
   const size_t NL = s.N / s.d[L - 1], N0 = s.N / s.d[0];
   float* q = p;
   size_t a16 = 4;
-  if (!big_in_smem) { q = gscratch; a16 = 64; }
+  if (big_in_smem <= 0) { q = gq; a16 = 64; }
   auto upg = [a16](size_t x) { return (x + a16 - 1) & ~(a16 - 1); };
   *Sbuf = q; q += upg((size_t)s.N);
   b.F = q; q += upg((size_t)s.N);

@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(1024) k_jtj_apply(JtjArgs a) {
 size_t dgn_smem_bytes_host(int L, const int* d, int R, int big_in_smem, int blk) {
   return dgn_smem_bytes(L, d, R, big_in_smem, blk);
 }
-size_t dgn_gscratch_floats_host(int L, const int* d, int R) { return dgn_gscratch_floats(L, d, R); }
+size_t dgn_gscratch_floats_host(int L, const int* d, int R, int big_in_smem) {
+  return dgn_gscratch_floats(L, d, R, big_in_smem);
+}
 
 cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st) {
   const void* fn = (L == 3) ? (const void*)k_dgn_core<3> : (const void*)k_dgn_core<4>;

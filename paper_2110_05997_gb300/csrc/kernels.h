@@ -83,7 +83,7 @@ inline int threads_for(const cpd_options* o, int n) {
   if (t > 1024) t = 1024;
   return t;
 }
-size_t dgn_gscratch_floats_host(int L, const int* d, int R);
+size_t dgn_gscratch_floats_host(int L, const int* d, int R, int big_in_smem = 0);
 
 cudaError_t launch_dgn_core(int L, const DgnArgs& a, int threads, size_t smem, cudaStream_t st);
 // The same solve by a cluster of csize CTAs (k_dgn_cluster.cu) for cores too
