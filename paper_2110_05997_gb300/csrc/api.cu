@@ -247,7 +247,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       PL("eig", launch_eig(ea, st));
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
       PL(l == 0 ? "project_T" : "project",
-         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st, p.err,
+                        o.timeout_cycles));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];
@@ -284,7 +285,8 @@ int run_compress(SolvePlan& p, const float* T, const cpd_options& o, cudaStream_
       View3 v{1, p.dims[l], c, l > 0 ? p.core_dims_dev : nullptr, l};
       float* out = (l == L - 1) ? p.core : bufs[l & 1];
       PL(l == 0 ? "project_T" : "project",
-         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st));
+         launch_project(cur, v, a_max, p.U + offU, p.core_dims_dev + l, p.P[l], out, st, p.err,
+                        o.timeout_cycles));
       cur = out;
       a_max *= p.P[l];
       offU += (size_t)p.idims[l] * p.P[l];
@@ -710,6 +712,7 @@ int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_op
   // write straight into the caller's buffers
   p.U = U_out; p.sigma = sigma_out; p.core = core_out;
   cudaStream_t st = as_stream(stream);
+  CK(cudaMemsetAsync(p.err, 0, sizeof(int), st));
   int rc = run_compress(p, T, o, st);
   if (rc != CPD_OK) return rc;
   if (core_dims_out) {

@@ -19,7 +19,8 @@ __device__ __forceinline__ long long view_a(const View3& v) {
 // ---- Gram on CUDA cores --------------------------------------------------------
 // G[j, j'] += sum_q X[q, j] X[q, j'], q = (i, k) over the (a, c) indices of
 // the (a, b, c) view, X[q, j] = T[i + a j + a b k].  CTA = one 64x64 tile of
-// the upper triangle x one K-split; 256 threads, 4x4 outputs each.
+// the upper triangle x one K-split; 256 threads, 4x4 outputs each; the
+// K-step's 16 rows q are loaded along the contiguous index.
 constexpr int kGT = 64, kGK = 16;
 
 __global__ void __launch_bounds__(256) k_gram_simt(const float* __restrict__ T, View3 v,
@@ -46,7 +47,9 @@ __global__ void __launch_bounds__(256) k_gram_simt(const float* __restrict__ T, 
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
-      const int kk = e / kGT, jj = e - kk * kGT;
+      // consecutive threads on the contiguous index: j when a = 1, else q
+      // (runs of a consecutive i)
+      const int kk = a == 1 ? e / kGT : e % kGK, jj = a == 1 ? e - kk * kGT : e / kGK;
       const long long base = qoff[kk];
       float xa = 0.f, xb = 0.f;
       if (base >= 0) {
@@ -85,7 +88,7 @@ cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G,
   const int ntile = (int)((v.b + kGT - 1) / kGT);
   const int npair = ntile * (ntile + 1) / 2;
   const long long K = a_max * v.c;
-  long long splits = (2 * 152 + npair - 1) / npair;
+  long long splits = (8 * 152 + npair - 1) / npair;     // eight CTAs per SM hide the load latency
   const long long maxs = (K + 255) / 256;
   if (splits > maxs) splits = maxs;
   if (splits < 1) splits = 1;
@@ -273,8 +276,95 @@ __global__ void __launch_bounds__(256) k_project_gen(const float* __restrict__ T
   }
 }
 
+// Later modes (a > 1): one thread per (i, k), consecutive threads on
+// consecutive i, so that the loads T(i, j, k) and the stores Y(i, r, k) of a
+// warp are contiguous runs.  A CTA of 256 threads holds Q = 256 / JS pairs
+// and splits the j range JS ways (each warp 32 consecutive pairs of one
+// split); the JS partial sums of a pair are added in shared memory, split
+// order.  U is held j-major (RP floats per j, zero beyond the rank).
+template <int RP, int JS>
+__global__ void __launch_bounds__(256) k_project_mid(const float* __restrict__ T, View3 v,
+                                                     const float* __restrict__ U, const int* dev_rank,
+                                                     float* Y) {
+  constexpr int Q = 256 / JS;
+  extern __shared__ __align__(16) float sm[];
+  const long long a = view_a(v), b = v.b, c = v.c;
+  float* Ut = sm;                                   // b x RP
+  float* part = Ut + (size_t)b * RP;                // JS x RP x Q partial sums
+  const int rk = *dev_rank;
+  for (long long e = threadIdx.x; e < b * RP; e += 256) {
+    const long long j = e / RP;
+    const int p = (int)(e - j * RP);
+    Ut[e] = p < rk ? U[(size_t)p * b + j] : 0.f;
+  }
+  __syncthreads();
+  const int split = threadIdx.x / Q, qq = threadIdx.x - split * Q;
+  const long long n = a * c, q = (long long)blockIdx.x * Q + qq;
+  const long long k = q / a, i = q - k * a;
+  float acc[RP];
+#pragma unroll
+  for (int p = 0; p < RP; ++p) acc[p] = 0.f;
+  if (q < n) {
+    const float* t = T + i + a * b * k;
+    const long long j1 = (split + 1) * b / JS;
+#pragma unroll 4
+    for (long long j = split * b / JS; j < j1; ++j) {
+      const float x = __ldg(t + a * j);
+      const float4* u4 = reinterpret_cast<const float4*>(Ut + j * RP);
+#pragma unroll
+      for (int g = 0; g < RP / 4; ++g) {
+        const float4 u = u4[g];
+        acc[4 * g] = fmaf(u.x, x, acc[4 * g]);
+        acc[4 * g + 1] = fmaf(u.y, x, acc[4 * g + 1]);
+        acc[4 * g + 2] = fmaf(u.z, x, acc[4 * g + 2]);
+        acc[4 * g + 3] = fmaf(u.w, x, acc[4 * g + 3]);
+      }
+    }
+  }
+  if constexpr (JS > 1) {
+#pragma unroll
+    for (int p = 0; p < RP; ++p) part[(split * RP + p) * Q + qq] = acc[p];
+    __syncthreads();
+    if (split == 0) {
+#pragma unroll
+      for (int p = 0; p < RP; ++p)
+        for (int s = 1; s < JS; ++s) acc[p] += part[(s * RP + p) * Q + qq];
+    }
+  }
+  if (split == 0 && q < n) {
+    float* y = Y + i + a * (long long)rk * k;
+#pragma unroll
+    for (int p = 0; p < RP; ++p)
+      if (p < rk) y[a * p] = acc[p];
+  }
+}
+
+template <int RP>
+cudaError_t launch_project_mid_rp(const float* T, View3 v, long long n_max, const float* U, const int* dev_rank,
+                                  float* Y, cudaStream_t st) {
+  int js = 1;
+  while (js < 8 && n_max * js < 152ll * 1024) js *= 2;
+  const size_t smem = ((size_t)v.b * RP + (size_t)256 * RP) * sizeof(float);
+  const long long q = 256 / js, blocks = (n_max + q - 1) / q;
+  if (blocks < 1 || blocks >= (1ll << 31)) return cudaErrorInvalidValue;
+  auto run = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, 256, smem, st>>>(T, v, U, dev_rank, Y);
+    count_launch();
+    return cudaGetLastError();
+  };
+  if (js == 1) return run(k_project_mid<RP, 1>);
+  if (js == 2) return run(k_project_mid<RP, 2>);
+  if (js == 4) return run(k_project_mid<RP, 4>);
+  return run(k_project_mid<RP, 8>);
+}
+
 cudaError_t launch_project(const float* T, View3 v, long long a_max, const float* U,
-                           const int* dev_rank, int rmax, float* Y, cudaStream_t st) {
+                           const int* dev_rank, int rmax, float* Y, cudaStream_t st, int* err,
+                           long long budget) {
+  if (v.a_host == 1 && v.dev_ranks == nullptr && project_tc_supported(v.b, v.c, rmax, T))
+    return launch_project_tc(T, v.b, v.c, U, dev_rank, rmax, Y, st, err, budget);
   if (v.a_host == 1 && v.dev_ranks == nullptr && rmax <= 16) {
     const int rp = rmax <= 4 ? 4 : rmax <= 8 ? 8 : rmax <= 12 ? 12 : 16;
     const size_t smem = ((size_t)v.b * rp + (size_t)kPC * (v.b + 1)) * sizeof(float);
@@ -297,6 +387,13 @@ cudaError_t launch_project(const float* T, View3 v, long long a_max, const float
       count_launch();
       return cudaGetLastError();
     }
+  }
+  if (rmax <= 16 && (size_t)v.b * 16 * sizeof(float) <= 160 * 1024) {
+    const long long n_max = a_max * v.c;
+    if (rmax <= 4) return launch_project_mid_rp<4>(T, v, n_max, U, dev_rank, Y, st);
+    if (rmax <= 8) return launch_project_mid_rp<8>(T, v, n_max, U, dev_rank, Y, st);
+    if (rmax <= 12) return launch_project_mid_rp<12>(T, v, n_max, U, dev_rank, Y, st);
+    return launch_project_mid_rp<16>(T, v, n_max, U, dev_rank, Y, st);
   }
   long long n = a_max * v.c;             // one warp per (i, k)
   long long blocks = (n + 7) / 8;

@@ -137,9 +137,17 @@ struct EigArgs {
 };
 cudaError_t launch_eig(const EigArgs& a, cudaStream_t st);
 size_t eig_work_floats(int I, int P);
-// Y(a, r, c) = sum_j U[j, r] T(a, j, c), r < rank (device) <= rmax.
+// Y(a, r, c) = sum_j U[j, r] T(a, j, c), r < rank (device) <= rmax.  The first
+// mode (a = 1) runs on tensor cores when project_tc_supported (err / budget:
+// see RefinePassArgs).
 cudaError_t launch_project(const float* T, View3 v, long long a_max, const float* U,
-                           const int* dev_rank, int rmax, float* Y, cudaStream_t st);
+                           const int* dev_rank, int rmax, float* Y, cudaStream_t st,
+                           int* err = nullptr, long long budget = 0);
+// First-mode projection on TF32 tensor cores with the three-product split
+// (k_project_tc.cu): 32 <= I <= 256, I % 4 == 0, c >= 128, rmax <= 16, T 16-byte aligned.
+bool project_tc_supported(long long I, long long c, int rmax, const float* T);
+cudaError_t launch_project_tc(const float* T, long long I, long long c, const float* U, const int* dev_rank,
+                              int rmax, float* Y, cudaStream_t st, int* err = nullptr, long long budget = 0);
 // Pack the truncated core (dims from the device) from a buffer laid out with
 // the same truncated dims: a copy (kept separate for clarity of ownership).
 cudaError_t launch_copy_f32(const float* src, float* dst, long long n, cudaStream_t st);

@@ -61,8 +61,16 @@ def _align_compress(Ug, Sg, Uo, So):
     return [A * s[None, :] for A, s in zip(Ug, signs)], S
 
 
+# The first-mode projection runs on TF32 tensor cores (three-product split)
+# for 32 <= I1 <= 256, I1 % 4 == 0, at least 128 columns and ranks <= 16:
+# one to eight 32-float K chunks with a ragged last chunk (I1 = 36, 100, 200),
+# full chunks (128, 256), a ragged last tile of columns (64 x 7 x 19 = 133
+# columns), order 4; the other shapes take the CUDA-core kernels.  The later
+# modes split the j range 8, 2 and 1 ways by the number of (i, k) pairs.
 CASES = [((30, 25, 20), 4, 0.0, 1e-4), ((100, 60, 45), 5, 0.5, 1e-4), ((16, 14, 12, 10), 3, 0.0, 1e-4),
-         ((41, 80, 7), 6, 0.3, 1e-3), ((12, 50, 50, 9), 4, 0.0, 1e-4)]
+         ((41, 80, 7), 6, 0.3, 1e-3), ((12, 50, 50, 9), 4, 0.0, 1e-4), ((128, 40, 30), 8, 0.0, 1e-4),
+         ((200, 30, 25), 10, 0.2, 1e-4), ((36, 33, 20, 6), 12, 0.0, 1e-4), ((256, 20, 9), 16, 0.0, 1e-4),
+         ((64, 7, 19), 3, 0.0, 1e-4), ((40, 40, 100, 100), 16, 0.0, 1e-4), ((40, 40, 100, 100), 15, 0.0, 1e-4)]
 
 
 @pytest.mark.parametrize("st", [1, 0])
