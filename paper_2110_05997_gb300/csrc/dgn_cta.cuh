@@ -98,7 +98,8 @@ __device__ void init_factors(const Shape& s, const Bufs& b, int mode, const floa
       for (int e = threadIdx.x; e < s.N; e += blockDim.x) {
         bool used = false;
         for (int t = 0; t < r; ++t) used |= (chosen[t] == e);
-        const float v = fabsf(b.S[e]);
+        float v = fabsf(b.S[e]);
+        if (!(v == v)) v = -0.5f;              // a NaN entry is still a valid choice
         if (!used && (v > best || (v == best && e < bi))) { best = v; bi = e; }
       }
       block_argmax(best, bi, b.red);

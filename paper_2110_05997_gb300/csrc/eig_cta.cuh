@@ -572,11 +572,13 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) lam[j] = (float)H[j * m + j];
   __syncthreads();
-  // order by |lambda| descending (stable)
+  // order by |lambda| descending (stable); a NaN ranks below every number, so
+  // that the positions are a permutation whatever the input (a poisoned Gram)
+  auto key = [](float x) { const float v = fabsf(x); return v == v ? v : -1.f; };
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     int p = 0;
-    const float lj = fabsf(lam[j]);
-    for (int t = 0; t < m; ++t) { const float lt = fabsf(lam[t]); p += (lt > lj || (lt == lj && t < j)) ? 1 : 0; }
+    const float lj = key(lam[j]);
+    for (int t = 0; t < m; ++t) { const float lt = key(lam[t]); p += (lt > lj || (lt == lj && t < j)) ? 1 : 0; }
     order[p] = j;
   }
   __syncthreads();
@@ -586,7 +588,8 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     const float* q = Q + j * I;
     float best = -1.f; int bi = 0x7fffffff;
     for (int i = threadIdx.x & 31; i < I; i += 32) {
-      const float x = fabsf(q[i]);
+      float x = fabsf(q[i]);
+      if (!(x == x)) x = -0.5f;                 // a NaN still yields a valid index
       if (x > best || (x == best && i < bi)) { best = x; bi = i; }
     }
 #pragma unroll

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tc(const __grid_constan
   };
 
   int issued = 0, committed = 0;         // issuer: chunks copied / whose MMAs were committed
+  int acc_tile = -1;                     // issuer: last tile whose accumulator was committed
   if (tid < kConv) {
     // ---- split: stage -> (hi, lo) buffer; warps 0-3 also store finished tiles
     bool ok = true;
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tc(const __grid_constan
         mma_tf32(dt + 2 * kN, sw128_desc(alo + ko), sw128_desc(bb + ko), idesc, acc);
       }
       mma_commit(bar_done + 8u * (uint32_t)ob);
-      if (ch == nch - 1) mma_commit(bar_acc + 8u * (uint32_t)(tl % kAcc));
+      if (ch == nch - 1) { mma_commit(bar_acc + 8u * (uint32_t)(tl % kAcc)); acc_tile = tl; }
       committed = j + 1;
     }
   }
@@ -290,6 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tc(const __grid_constan
       (void)mbar_wait_cycles(bar_done + 8u * (uint32_t)(jl % kOpBufs), (uint32_t)((jl / kOpBufs) & 1),
                              failed ? kDrainBudget : a.budget);
     }
+    if (failed && acc_tile >= 0)           // and its last accumulator arrive has landed
+      (void)mbar_wait_cycles(bar_acc + 8u * (uint32_t)(acc_tile % kAcc), (uint32_t)((acc_tile / kAcc) & 1),
+                             kDrainBudget);
   }
   fence_before_sync();
   __syncthreads();
