@@ -148,6 +148,7 @@ def solve_options(cpd, args, extra):
 STAGE_SOURCES = {
     "dgn_core": ["k_dgn.cu", "k_dgn_cluster.cu", "dgn_cta.cuh", "solver.cuh", "common.cuh", "kernels.h"],
     "gram_bf16_tc": ["k_gram_tc.cu", "tc_common.cuh", "kernels.h"],
+    "project_T": ["k_project_tc.cu", "tc_common.cuh", "kernels.h"],
     "refine_pass": ["k_refine_tc.cu", "tc_common.cuh", "k_refine_pass3.cu", "k_refine_pass4.cu", "refine_pass.cuh",
                     "solver.cuh", "common.cuh", "kernels.h"],
 }
@@ -190,6 +191,26 @@ def algorithmic(stage: str, dims, R: int, info: dict, per_launch_ms: float, pk: 
     fp32_peak_tf = sms * 128 * 2 * mhz * 1e6 / 1e12          # FP32 FMA pipes, all SMs
     if stage == "refine_pass":
         nbytes = 4.0 * N + 4.0 * 2 * R * sum(dims)              # read T, read W, write G
+        ach = nbytes / (per_launch_ms * 1e-3) / 1e9
+        return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    algorithmic_per_launch=nbytes)
+    if stage == "project_T":
+        # first-mode projection: read T, write the rank-P1 partial core
+        P1 = int(info["core_dims"][0])
+        nbytes = 4.0 * N + 4.0 * P1 * (N // I1)
+        ach = nbytes / (per_launch_ms * 1e-3) / 1e9
+        return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    algorithmic_per_launch=nbytes, flops=2.0 * P1 * N)
+    if stage == "project":
+        # later-mode projections of the sequentially truncated tensor: read the
+        # mode-l input, write its projection, averaged over those launches
+        cd = [int(d) for d in info["core_dims"] if d > 0]
+        bs = []
+        for l in range(1, len(dims)):
+            nin = float(np.prod(cd[:l])) * float(np.prod([int(d) for d in dims[l:]]))
+            nout = float(np.prod(cd[:l + 1])) * float(np.prod([int(d) for d in dims[l + 1:]]))
+            bs.append(4.0 * (nin + nout))
+        nbytes = sum(bs) / len(bs)
         ach = nbytes / (per_launch_ms * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
                     algorithmic_per_launch=nbytes)
@@ -419,7 +440,7 @@ def run_ours(args, rank, world, local_rank):
     # the same roofline entry for the other stages that have a bound
     stage_roofs = {}
     for k, v in prof.items():
-        if k == dom[0] or k not in ("gram_bf16_tc", "gram_fp32", "refine_pass"):
+        if k == dom[0] or k not in ("gram_bf16_tc", "gram_fp32", "refine_pass", "project_T", "project"):
             continue
         n = v["launches"]
         if k == "refine_pass":

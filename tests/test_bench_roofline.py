@@ -27,6 +27,23 @@ def test_tensor_core_gram_reads_the_tensor_once():
     assert r["flops"] == 2.0 * 200 * 200 ** 3
 
 
+def test_first_mode_projection_reads_t_and_writes_the_partial_core():
+    import bench
+    r = bench.algorithmic("project_T", (200, 200, 200), 10, INFO, 0.04, PK, 2070)
+    # T once, then the 10 x 200 x 200 result of the first truncation step
+    assert r["algorithmic_per_launch"] == 4.0 * 200 ** 3 + 4.0 * 10 * 200 * 200
+    assert r["bound"] == "hbm"
+
+
+def test_later_projections_follow_the_sequential_truncation():
+    import bench
+    r = bench.algorithmic("project", (200, 200, 200), 10, INFO, 0.01, PK, 2070)
+    # mode 2: 10x200x200 -> 10x10x200; mode 3: 10x10x200 -> 10x10x10
+    m2 = 4.0 * (10 * 200 * 200 + 10 * 10 * 200)
+    m3 = 4.0 * (10 * 10 * 200 + 10 * 10 * 10)
+    assert abs(r["algorithmic_per_launch"] - (m2 + m3) / 2) < 1e-6
+
+
 @pytest.mark.parametrize("bf16,expected", [
     # modes 2 and 3 on the truncated 10x200x200 and 10x10x200 tensors
     (True, (2 * 200 * (10 * 200 * 200) + 2 * 200 * (10 * 10 * 200)) / 2),
