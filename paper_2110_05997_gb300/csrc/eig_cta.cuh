@@ -561,10 +561,15 @@ static __device__ void eig_run(const EigArgs& a, unsigned char* smem_raw) {
     // Rayleigh-Ritz: H = Q^T G Q, eig, U = Q V
     rayleigh(Q, Z, H, I, m);
     jacobi_eig(H, V, m, W1, W2, a.fp32_only == 0);
+    // U = Q V with V rounded to FP32 once (W1 is free again): a conversion
+    // from FP64 inside every FMA would run on the narrow FP64 pipe
+    float* Vs = reinterpret_cast<float*>(W1);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Vs[e] = (float)V[e];
+    __syncthreads();
     for (int e = threadIdx.x; e < I * m; e += blockDim.x) {
       const int j = e / I, i = e - j * I;
       float s = 0.f;
-      for (int k = 0; k < m; ++k) s = fmaf(Q[k * I + i], (float)V[k * m + j], s);
+      for (int k = 0; k < m; ++k) s = fmaf(Q[k * I + i], Vs[k * m + j], s);
       Z[e] = s;
     }
     __syncthreads();

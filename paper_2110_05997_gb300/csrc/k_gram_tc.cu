@@ -324,20 +324,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(TcArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
-// Co-resident clusters of kCluster CTAs for a dynamic shared-memory size,
-// queried once per (device, size).
-int max_clusters(int dev, size_t smem, const cudaLaunchConfig_t& cfg) {
+// Co-resident clusters of the configuration's cluster size for a dynamic
+// shared-memory size, queried once per (device, size, cluster size).
+int max_clusters(int dev, size_t smem, int cs, const cudaLaunchConfig_t& cfg) {
   static std::mutex mu;
-  static std::map<std::pair<int, size_t>, int> cache;
+  static std::map<std::pair<int, std::pair<size_t, int>>, int> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find({dev, smem});
+  const auto key = std::make_pair(dev, std::make_pair(smem, cs));
+  auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, k_gram_tc, &cfg) != cudaSuccess) {
     (void)cudaGetLastError();
     n = 0;
   }
-  cache[{dev, smem}] = n;
+  cache[key] = n;
   return n;
 }
 
@@ -382,26 +383,29 @@ cudaError_t launch_gram_bf16_tc(const float* T, long long I, long long C, float*
   a.stages = S;
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // clusters of kCluster CTAs when every CTA of every co-resident cluster gets
-  // at least one step; otherwise single-CTA clusters
+  // The cluster size (8, 4 or 2) that keeps the most SMs busy: clusters are
+  // placed within a GPC, so clusters of 8 leave the SMs of a GPC beyond a
+  // multiple of 8 idle (120 of 152 on GB300).  Larger clusters sum more of
+  // the partial Grams on chip, so ties go to the larger size; single-CTA
+  // clusters when none fits.  Every CTA must get at least one step.
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kCluster; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+  attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr; cfg.numAttrs = 1;
   int cs = 1, grid = (nsm > 0 ? nsm : 1);
-  cfg.gridDim = dim3(kCluster * ((nsm + kCluster - 1) / kCluster));
-  const int ncl = a.nk >= 2 * kCluster ? max_clusters(dev, smem, cfg) : 0;
-  if (ncl > 0) {
-    cs = kCluster;
-    grid = ncl * kCluster;
-    while (grid > a.nk) grid -= kCluster;
-  } else {
-    if (grid > a.nk) grid = a.nk;
+  for (int c = kCluster; c >= 2; c >>= 1) {
+    if (a.nk < 2 * c) continue;
+    attr[0].val.clusterDim.x = c;
+    cfg.gridDim = dim3(c * ((nsm + c - 1) / c));
+    const int ncl = max_clusters(dev, smem, c, cfg);
+    if (ncl * c > (cs == 1 ? 0 : grid)) { cs = c; grid = ncl * c; }
   }
+  while (grid > a.nk && grid > cs) grid -= cs;
+  if (cs == 1 && grid > a.nk) grid = a.nk;
   attr[0].val.clusterDim.x = cs;
   cfg.gridDim = dim3(grid);
   e = cudaLaunchKernelEx(&cfg, k_gram_tc, a);
