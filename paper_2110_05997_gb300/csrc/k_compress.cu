@@ -84,7 +84,123 @@ __global__ void __launch_bounds__(256) k_gram_simt(const float* __restrict__ T, 
     }
 }
 
+// Gram of a mode with b <= 128 columns: one CTA forms the whole b x b Gram
+// over a contiguous range of rows q (split K), NT x NT threads with an 8 x 8
+// register block each (tile width W = 8 NT >= b): per row q one 16-byte pair
+// of loads for the block's rows and one for its columns feed 64 FMAs.  The
+// K-step's 16 rows are loaded along the contiguous index (j when a = 1, else
+// q), the next step's loads in flight in registers during this step's FMAs
+// (double-buffered shared memory); the partial Gram is added into G with
+// float4 atomics (b % 4 == 0 and a 16-byte aligned G) or scalar ones.  Both
+// triangles are formed directly.
+constexpr int kSqK = 16;
+
+template <int NT>
+__global__ void __launch_bounds__(NT * NT) k_gram_sq(const float* __restrict__ T, View3 v, long long chunk,
+                                                      float* G, int vec4) {
+  constexpr int W = 8 * NT, LD = W + 4, NTH = NT * NT;
+  constexpr int PER = (kSqK * W + NTH - 1) / NTH;       // elements a thread loads per K-step
+  __shared__ __align__(16) float Xs[2][kSqK][LD];
+  const unsigned a = (unsigned)view_a(v), b = (unsigned)v.b;
+  const unsigned K = a * (unsigned)v.c;                // < 2^32: tensors hold at most 4e9 entries
+  const unsigned q0 = (unsigned)((long long)blockIdx.x * chunk);
+  const unsigned q1 = (unsigned)min((long long)q0 + chunk, (long long)K);
+  if (q0 >= q1) return;
+  const int tx = threadIdx.x % NT, ty = threadIdx.x / NT;
+  // element e of a K-step: row kk, column jj, along the contiguous index
+  auto load = [&](unsigned qb, float (&x)[PER]) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = threadIdx.x + t * NTH;
+      const int kk = a == 1 ? e / W : e % kSqK, jj = a == 1 ? e - kk * W : e / kSqK;
+      const unsigned q = qb + (unsigned)kk;
+      float val = 0.f;
+      if (e < kSqK * W && q < q1 && (unsigned)jj < b) {
+        const unsigned k = q / a, i = q - k * a;
+        val = __ldg(T + (size_t)i + (size_t)a * b * k + (size_t)a * jj);
+      }
+      x[t] = val;
+    }
+  };
+  auto store = [&](int buf, const float (&x)[PER]) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = threadIdx.x + t * NTH;
+      if (e < kSqK * W) {
+        const int kk = a == 1 ? e / W : e % kSqK, jj = a == 1 ? e - kk * W : e / kSqK;
+        Xs[buf][kk][jj] = x[t];
+      }
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) acc[u][w] = 0.f;
+  float x[PER];
+  load(q0, x);
+  store(0, x);
+  __syncthreads();
+  int buf = 0;
+  for (unsigned qb = q0; qb < q1; qb += kSqK) {
+    const bool more = qb + kSqK < q1;
+    if (more) load(qb + kSqK, x);                       // in flight during this step's FMAs
+#pragma unroll 4
+    for (int kk = 0; kk < kSqK; ++kk) {
+      const float4 r0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8]);
+      const float4 r1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8 + 4]);
+      const float4 c0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][tx * 8]);
+      const float4 c1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][tx * 8 + 4]);
+      const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc[u][w] = fmaf(rv[u], cv[w], acc[u][w]);
+    }
+    if (more) store(buf ^ 1, x);
+    __syncthreads();
+    buf ^= 1;
+  }
+  const int r0 = ty * 8;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const unsigned c = (unsigned)(tx * 8 + w);
+    if (c >= b) continue;
+    float* g = G + (size_t)b * c;
+    if (vec4 && (unsigned)(r0 + 8) <= b) {
+      atomicAdd(reinterpret_cast<float4*>(g + r0), make_float4(acc[0][w], acc[1][w], acc[2][w], acc[3][w]));
+      atomicAdd(reinterpret_cast<float4*>(g + r0 + 4), make_float4(acc[4][w], acc[5][w], acc[6][w], acc[7][w]));
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if ((unsigned)(r0 + u) < b) atomicAdd(g + r0 + u, acc[u][w]);
+    }
+  }
+}
+
+template <int NT>
+cudaError_t launch_gram_sq_t(const float* T, View3 v, long long a_max, float* G, cudaStream_t st) {
+  const long long K = a_max * v.c;
+  long long grid = 2 * 152;                          // two CTAs per SM, each a K range
+  const long long maxg = (K + 4 * kSqK - 1) / (4 * kSqK);
+  if (grid > maxg) grid = maxg;
+  if (grid < 1) grid = 1;
+  long long chunk = (K + grid - 1) / grid;
+  chunk = (chunk + kSqK - 1) / kSqK * kSqK;
+  grid = (K + chunk - 1) / chunk;
+  const int vec4 = (v.b % 4 == 0 && (reinterpret_cast<uintptr_t>(G) & 15u) == 0) ? 1 : 0;
+  k_gram_sq<NT><<<(unsigned)grid, NT * NT, 0, st>>>(T, v, chunk, G, vec4);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram_simt(const float* T, View3 v, long long a_max, float* G, cudaStream_t st) {
+  if (v.b <= 32) return launch_gram_sq_t<4>(T, v, a_max, G, st);
+  if (v.b <= 56) return launch_gram_sq_t<7>(T, v, a_max, G, st);
+  if (v.b <= 80) return launch_gram_sq_t<10>(T, v, a_max, G, st);
+  if (v.b <= 104) return launch_gram_sq_t<13>(T, v, a_max, G, st);
+  if (v.b <= 128) return launch_gram_sq_t<16>(T, v, a_max, G, st);
   const int ntile = (int)((v.b + kGT - 1) / kGT);
   const int npair = ntile * (ntile + 1) / 2;
   const long long K = a_max * v.c;
