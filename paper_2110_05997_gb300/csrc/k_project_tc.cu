@@ -89,14 +89,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 // Bounded wait on an mbarrier phase that also gives up once another role has
@@ -300,19 +292,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_project_tc(const __grid_constan
   if (warp == 0) tmem_dealloc(tmem, kAcc * kAccCols);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  });
-  return fn;
-}
-
 size_t ptc_smem(int nch, int S) {
   return 1024 + (size_t)S * kChunkBytes + (size_t)kOpBufs * 2 * kChunkBytes + (size_t)nch * 2 * kBBytes +
          8 * (kMaxStages + 2 * kOpBufs + kAcc) + 16 + (size_t)4 * kN * kOutLd * 4;
@@ -329,7 +308,7 @@ PtcCache g_ptc;
 
 bool project_tc_supported(long long I, long long c, int rmax, const float* T) {
   return I >= 32 && I <= 256 && (I % 4) == 0 && c >= kM && c < (1ll << 31) && rmax >= 1 && rmax <= kN &&
-         (reinterpret_cast<uintptr_t>(T) & 15u) == 0 && encoder() != nullptr;
+         (reinterpret_cast<uintptr_t>(T) & 15u) == 0 && tensor_map_encoder() != nullptr;
 }
 
 cudaError_t launch_project_tc(const float* T, long long I, long long c, const float* U, const int* dev_rank,
@@ -374,7 +353,7 @@ cudaError_t launch_project_tc(const float* T, long long I, long long c, const fl
   cuuint64_t gstride[1] = {(cuuint64_t)I * 4};
   cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kM};
   cuuint32_t estr[2] = {1, 1};
-  if (encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(T), gdim, gstride, box, estr,
+  if (tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(T), gdim, gstride, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;

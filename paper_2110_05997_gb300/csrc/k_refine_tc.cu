@@ -115,14 +115,6 @@ __device__ __forceinline__ void arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
 // x = hi + mid + lo, each BF16 (round to nearest): 24 significant bits.
 __device__ __forceinline__ void split3(float x, float& h, float& m, float& l) {
   h = __bfloat162float(__float2bfloat16_rn(x));
@@ -688,19 +680,6 @@ bool tc_plan(int L, const long long* dims, int R, TcPlan& p) {
   p.o_bar = (uint32_t)up(o, 8); o = p.o_bar + 8 * kNumBars + 16;
   p.smem = up(o, 16) + 1024;                 // + the alignment of the base to 1024 bytes
   return p.smem <= (size_t)227 * 1024;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  });
-  return fn;
 }
 
 struct TcLaunchCache {

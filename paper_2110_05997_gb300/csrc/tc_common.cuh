@@ -1,13 +1,19 @@
 // Shared plumbing of the tcgen05 (5th-generation tensor core) kernels:
 // shared-memory addresses, bounded mbarrier waits, the shared-memory matrix
 // descriptor of the 128-byte-swizzled K-major layout, the kind::f16
-// instruction descriptor, BF16 packing, and the tensor-memory allocation
-// and fence instructions.  Written from the PTX ISA's descriptions of
-// tcgen05.mma, tcgen05.alloc / dealloc, mbarrier and cp.async.bulk.
+// instruction descriptor, BF16 packing, the tensor-memory allocation and
+// fence instructions, the 2D tensor copy and the tensor-map encoder lookup.
+// Written from the PTX ISA's descriptions of tcgen05.mma, tcgen05.alloc /
+// dealloc, mbarrier and cp.async.bulk(.tensor).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 namespace cpdk {
 namespace tc {
@@ -197,6 +203,30 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t 
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// 2D tensor copy (TMA) of the box at coordinates (x, y) of the tensor map into
+// shared memory at `dst`, completed on the mbarrier `bar` (transaction bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// The driver's cuTensorMapEncodeTiled, looked up once (nullptr when absent).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
 }
 
 // Arrive once on the mbarrier `bar` when every tcgen05.mma this thread issued
