@@ -120,10 +120,10 @@ WORKLOADS = {
     "full400": dict(gen=lambda: dict(T=synth.planted(7, (400, 400, 400), 10, 0.0, 1e-5, np.float32)[0], R=10),
                     opts=dict(compress=0, init="random", seed=5, gram_precision="fp32", refine_maxiter=0),
                     name="dgn_uncompressed_400x400x400_r10_noise1e-5_random_start_seed5"),
-    # the same with a first mode the tensor-core pass takes (I1 <= 256)
-    "full256": dict(gen=lambda: dict(T=synth.planted(8, (256, 512, 512), 10, 0.0, 1e-5, np.float32)[0], R=10),
-                    opts=dict(compress=0, init="random", seed=5, gram_precision="fp32", refine_maxiter=0),
-                    name="dgn_uncompressed_256x512x512_r10_noise1e-5_random_start_seed5"),
+    # the same on the 100^4 rank-15 tensor, a shape the tensor-core pass takes
+    "full_order4": dict(gen=synth.c3_order4, opts=dict(compress=0, init="random", seed=0, gram_precision="fp32",
+                                                       refine_maxiter=0),
+                        name="dgn_uncompressed_100x100x100x100_r15_noise1e-5_random_start"),
 }
 
 
@@ -643,7 +643,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gram", choices=["fp32", "bf16"], default="bf16")
-    workloads = ["order4", "compressed200", "full400", "full256", "batch", "initnet"]
+    workloads = ["order4", "compressed200", "full400", "full_order4", "batch", "initnet"]
     ap.add_argument("--workload", choices=workloads, default="order4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
