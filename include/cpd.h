@@ -165,6 +165,14 @@ size_t cpd_workspace_size(int L, const int64_t* dims, int R, const cpd_options* 
  *               (of the sequential unfoldings under ST-MLSVD)
  *   core_dims_out host, L ints: R~_l (synchronises the stream)
  * Singular vectors are sign-normalised (largest-|.| entry positive).
+ * Arithmetic: the Grams in FP32 (the first mode's in BF16 on tensor cores
+ * with opts->gram_precision = CPD_GRAM_BF16, FP32 accumulation); the first
+ * mode's projection on TF32 tensor cores with both operands split into two
+ * TF32 parts (FP32-accurate: |error| <= 2^-21 sum |t u|) when 32 <= I1 <= 256,
+ * I1 % 4 == 0, N / I1 >= 128, P_1 <= 16 and T is 16-byte aligned, else and
+ * for the other modes on the CUDA cores in FP32.  A bounded pipeline wait of
+ * a tensor-core kernel that runs out (opts->timeout_cycles) leaves NaN in
+ * its output.
  */
 int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_options* opts,
                  float* U_out, float* core_out, float* sigma_out, int* core_dims_out,
@@ -174,9 +182,12 @@ int cpd_compress(const float* T, int L, const int64_t* dims, int R, const cpd_op
  * cpd_dgn_solve — the whole method of Fig. "tensorfox-flow" (Sec. 4.1):
  * compression (if opts->compress), initialisation, damped Gauss-Newton on the
  * core (Sec. 4.1.3: residual, MTTKRP gradient, Hadamard-of-Gram Pi matrices,
- * matrix-free J^T J v of Theorem "Hv" inside Jacobi-preconditioned CG with the
- * diagonal regulariser of Sec. 4.8), uncompression (Sec. 4.1.4), optional
- * refinement iterations on T, and output normalisation.
+ * matrix-free J^T J v of Theorem "Hv" inside Jacobi- or block-Jacobi-
+ * preconditioned CG with the diagonal regulariser of Sec. 4.8), uncompression
+ * (Sec. 4.1.4), optional refinement iterations on T, and output normalisation.
+ * Without compression, an FP32 tensor of at least 2^20 entries with a random
+ * or given start runs every dGN iteration as one pass over T plus a
+ * single-CTA step (the refinement machinery; same limits as refinement).
  *   T          device, element type `dtype` (CPD_F64 only with compress = 0)
  *   W0         device, FP32, stacked I_l x R blocks (INIT_GIVEN), else NULL
  *   W_out      device, FP32, stacked I_l x R blocks with unit columns
