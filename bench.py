@@ -411,25 +411,55 @@ def run_ours(args, rank, world, local_rank):
         prof = cpd.cpd_profile_read()
         cpd.cpd_profile_enable(False)
 
-        # end to end through the C ABI with host buffers: H2D of T, solve, D2H of W and lambda
+        # end to end through the C ABI with host buffers: every step copies its
+        # tensor from pinned host memory (H2D), solves it and reads W and lambda
+        # back (D2H).  T is double-buffered on the device: the copy of step k+1
+        # runs on a copy stream while step k is solved, as a caller streaming
+        # tensors through the library would.  One span of CUDA events on the
+        # compute stream brackets all K steps (the copy stream starts after the
+        # opening event); the 400 MB inputs exceed L2, so no flush is needed.
         Th = torch.from_numpy(T_flat).pin_memory()
-        Tdev2 = torch.empty_like(Td)
+        Tbuf = [torch.empty_like(Td), torch.empty_like(Td)]
+        copy_stream = torch.cuda.Stream(device=dev)
         n_out = R * sum(dims)
         Wh = torch.empty(n_out, dtype=torch.float32).pin_memory()
         lh = torch.empty(R, dtype=torch.float32).pin_memory()
 
-        def e2e_step():
-            Tdev2.copy_(Th, non_blocking=True)
-            W2, lam2, _, _ = cpd.cpd_dgn_solve(Tdev2, dims, R, opts, stream=stream, workspace=ws,
-                                               want_info=False)
-            Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
-            lh.copy_(lam2, non_blocking=True)
-        e2e_step()
+        def e2e_run(K):
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            copied = [torch.cuda.Event(), torch.cuda.Event()]
+            used = [torch.cuda.Event(), torch.cuda.Event()]
+            torch.cuda.synchronize()
+            t0.record(stream)
+            copy_stream.wait_event(t0)
+            with torch.cuda.stream(copy_stream):
+                Tbuf[0].copy_(Th, non_blocking=True)
+            copied[0].record(copy_stream)
+            for k in range(K):
+                b = k & 1
+                if k + 1 < K:
+                    nb = b ^ 1
+                    if k >= 1:
+                        copy_stream.wait_event(used[nb])       # step k-1 has read that buffer
+                    with torch.cuda.stream(copy_stream):
+                        Tbuf[nb].copy_(Th, non_blocking=True)
+                    copied[nb].record(copy_stream)
+                stream.wait_event(copied[b])
+                W2, lam2, _, _ = cpd.cpd_dgn_solve(Tbuf[b], dims, R, opts, stream=stream, workspace=ws,
+                                                   want_info=False)
+                used[b].record(stream)
+                Wh.copy_(torch.cat([w.t().reshape(-1) for w in W2]), non_blocking=True)
+                lh.copy_(lam2, non_blocking=True)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            return t0.elapsed_time(t1)
+        e2e_run(2)                                             # captures the graphs of both buffers
         start_barrier(world)
-        e2e_ms, _ = _timed_steps(torch, e2e_step, flush, stream, args.steps)
+        e2e_ms = e2e_run(args.steps)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e = dict(value=whole_job_value(1, args.steps, world, e2e_ms), unit=UNIT,
-               h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4))
+               h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4),
+               pipeline="H2D of step k+1 on a copy stream during step k's solve (T double-buffered)")
 
     if rank != 0:
         return 0
