@@ -459,7 +459,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e = dict(value=whole_job_value(1, args.steps, world, e2e_ms), unit=UNIT,
                h2d_bytes_per_step=int(Th.numel() * 4), d2h_bytes_per_step=int((n_out + R) * 4),
-               pipeline="H2D of step k+1 on a copy stream during step k's solve (T double-buffered)")
+               pipeline="H2D of step k+1 on a copy stream during step k's solve (T double-buffered)",
+               l2="no flush: every step's input (copied from the host) is larger than L2")
 
     if rank != 0:
         return 0
